@@ -1,0 +1,277 @@
+"""CPU oracle for the tracking-enabled island-model GA (arXiv 2404.10861).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg are the only callers.  The product
+package never imports this module, and this module never imports the
+product package; they share no code.
+
+The arithmetic lives in ``hsga_oracle.c`` (plain C, single-threaded, built
+with gcc by :func:`build`); this file only marshals numpy arrays through
+ctypes.  Every function names the step of the paper's generational cycle
+(section "Asynchronous Island-model Genetic Algorithm") that it follows; the
+C source states the readings used where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hsga_oracle.c")
+_LIB = os.path.join(_HERE, "libhsga_oracle.so")
+
+STEADY, TILTED, STRETCHED, TRIVIAL, NONE = 0, 1, 2, 3, 4
+POLICY_NAMES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
+                "trivial": TRIVIAL, "none": NONE}
+REC_WORDS = 6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable C: x86_64 and aarch64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint32), ("cols", ctypes.c_uint32),
+                ("n", ctypes.c_uint32), ("tournament", ctypes.c_uint32),
+                ("policy", ctypes.c_uint32), ("bits", ctypes.c_uint32),
+                ("W", ctypes.c_uint32), ("interval", ctypes.c_uint32),
+                ("p_ben", ctypes.c_double), ("p_del", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+@dataclass
+class Config:
+    """One run's parameters, in the paper's vocabulary.
+
+    rows x cols toroidal island grid, ``n`` agents per island, tournament size,
+    surface policy, differentia bit width (S = 64 / bits surface sites),
+    sites per level W (tilted / stretched), migration interval (0 = none),
+    beneficial / deleterious mutation probabilities and the Philox seed.
+    """
+    rows: int = 4
+    cols: int = 4
+    n: int = 32
+    tournament: int = 2
+    policy: int = STEADY
+    bits: int = 1
+    W: int = 2
+    interval: int = 1
+    p_ben: float = 0.0
+    p_del: float = 0.0
+    seed: int = 1
+
+    @property
+    def islands(self) -> int:
+        return self.rows * self.cols
+
+    @property
+    def agents(self) -> int:
+        return self.rows * self.cols * self.n
+
+    @property
+    def S(self) -> int:
+        return 64 // self.bits
+
+    def _c(self) -> _Cfg:
+        return _Cfg(self.rows, self.cols, self.n, self.tournament, self.policy,
+                    self.bits, self.W, self.interval, self.p_ben, self.p_del,
+                    self.seed)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        u32, u64, i32, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
+        P = ctypes.POINTER
+        _lib.orc_philox4x32_10.argtypes = [u32, u32, P(u32), P(u32)]
+        _lib.orc_philox4x64_10.argtypes = [u64, u64, P(u64), P(u64)]
+        _lib.orc_site.argtypes = [u32, u32, u32, u64]
+        _lib.orc_site.restype = u32
+        _lib.orc_lookup.argtypes = [u32, u32, u32, u64, P(i64)]
+        _lib.orc_neighbour.argtypes = [P(_Cfg), u32, u32]
+        _lib.orc_neighbour.restype = u32
+        _lib.orc_emigrate.argtypes = [P(_Cfg), u32, P(u32), P(u32), P(u64), u64, P(u32)]
+        _lib.orc_immigrate.argtypes = [P(_Cfg), u32, P(u32), P(i32), ctypes.c_void_p,
+                                       P(u32), P(u64), P(u32), u64, ctypes.c_void_p]
+        _lib.orc_select.argtypes = [P(_Cfg), u32, P(u32), ctypes.c_void_p, P(u32), P(u64),
+                                    ctypes.c_void_p, u64, u64, P(u32), P(u64), ctypes.c_void_p]
+        _lib.orc_run_grid.argtypes = [P(_Cfg), P(u32), P(u64), u64, u64, ctypes.c_int,
+                                      ctypes.c_void_p]
+        _lib.orc_run_grid.restype = ctypes.c_int
+        _lib.orc_migrate_grid.argtypes = [P(_Cfg), P(u32), P(u64), u64]
+        _lib.orc_migrate_grid.restype = ctypes.c_int
+        _lib.orc_run_cone.argtypes = [P(_Cfg), u32, u32, u32, u64, u64, u32, P(u32), P(u64)]
+        _lib.orc_run_cone.restype = ctypes.c_int
+        _lib.orc_sample_grid.argtypes = [P(_Cfg), P(u32), P(u64), u64, u32, P(u32),
+                                         ctypes.c_void_p]
+        _lib.orc_sample_grid.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _vp(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+# ----------------------------------------------------------------- RNG ---
+
+def philox4x32(key, counter) -> np.ndarray:
+    """Philox4x32-10 block (Salmon et al. SC'11); key = (k0, k1)."""
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(int(key[0]), int(key[1]), _p(c, ctypes.c_uint32),
+                            _p(out, ctypes.c_uint32))
+    return out
+
+
+def philox4x64(key, counter) -> np.ndarray:
+    """The same rounds at 64-bit words (pins the round structure)."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64_10(int(key[0]), int(key[1]), _p(c, ctypes.c_uint64),
+                            _p(out, ctypes.c_uint64))
+    return out
+
+
+# ------------------------------------------------------------- surface ---
+
+def site(policy: int, S: int, W: int, T: int) -> int:
+    """Site written by deposition T (S means: discarded)."""
+    return int(lib().orc_site(policy, S, W, T))
+
+
+def lookup(policy: int, S: int, W: int, T: int) -> np.ndarray:
+    """Deposition time held by every site after T depositions (-1 = empty)."""
+    out = np.zeros(S, dtype=np.int64)
+    lib().orc_lookup(policy, S, W, T, _p(out, ctypes.c_int64))
+    return out
+
+
+# ------------------------------------------------------------------ GA ---
+
+def founders(cfg: Config):
+    """Founding population: every trait 0, every surface empty (all zero)."""
+    return (np.zeros(cfg.agents, dtype=np.uint32),
+            np.zeros(cfg.agents, dtype=np.uint64))
+
+
+def run(cfg: Config, trait=None, surf=None, G0: int = 0, generations: int = 1,
+        premigrated: bool = False, track_parents: bool = False):
+    """Synchronous run of ``generations`` full cycles from generation G0.
+
+    Returns (trait, surf, parents); parents is (generations, agents) uint64 of
+    pre-migration parent indices, or None.
+    """
+    if trait is None:
+        trait, surf = founders(cfg)
+    trait = np.ascontiguousarray(trait, dtype=np.uint32).copy()
+    surf = np.ascontiguousarray(surf, dtype=np.uint64).copy()
+    parents = (np.zeros((generations, cfg.agents), dtype=np.uint64)
+               if track_parents else None)
+    c = cfg._c()
+    rc = lib().orc_run_grid(ctypes.byref(c), _p(trait, ctypes.c_uint32),
+                            _p(surf, ctypes.c_uint64), G0, generations,
+                            int(premigrated), _vp(parents))
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return trait, surf, parents
+
+
+def migrate(cfg: Config, trait, surf, G: int):
+    """Explicit emigrate + immigrate (steps a1, a2) of generation G."""
+    trait = np.ascontiguousarray(trait, dtype=np.uint32).copy()
+    surf = np.ascontiguousarray(surf, dtype=np.uint64).copy()
+    c = cfg._c()
+    if lib().orc_migrate_grid(ctypes.byref(c), _p(trait, ctypes.c_uint32),
+                              _p(surf, ctypes.c_uint64), G) != 0:
+        raise MemoryError("oracle migrate failed")
+    return trait, surf
+
+
+def run_cone(cfg: Config, row: int, col: int, generations: int, G0: int = 0,
+             trait0: int = 0, surf0: int = 0):
+    """One island's agents after ``generations`` cycles from a uniform state,
+    computed on its dependency cone only (exact at any torus size)."""
+    t = np.zeros(cfg.n, dtype=np.uint32)
+    s = np.zeros(cfg.n, dtype=np.uint64)
+    c = cfg._c()
+    rc = lib().orc_run_cone(ctypes.byref(c), row, col, trait0, surf0, G0,
+                            generations, _p(t, ctypes.c_uint32),
+                            _p(s, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError(f"cone run failed ({rc})")
+    return t, s
+
+
+def sample(cfg: Config, trait, surf, G: int, k: int):
+    """Step a7: k sampled genomes (k x 4 words) and their (island, slot)."""
+    trait = np.ascontiguousarray(trait, dtype=np.uint32)
+    surf = np.ascontiguousarray(surf, dtype=np.uint64)
+    words = np.zeros((k, 4), dtype=np.uint32)
+    where = np.zeros((k, 2), dtype=np.uint32)
+    c = cfg._c()
+    rc = lib().orc_sample_grid(ctypes.byref(c), _p(trait, ctypes.c_uint32),
+                               _p(surf, ctypes.c_uint64), G, k,
+                               _p(words, ctypes.c_uint32), _vp(where))
+    if rc == -2:
+        raise ValueError("k exceeds the number of islands")
+    if rc != 0:
+        raise MemoryError("oracle sample failed")
+    return words, where
+
+
+# ------------------------------------------- pieces for band decomposition ---
+
+def emigrate(cfg: Config, gid, trait, surf, G: int) -> np.ndarray:
+    """Step a1 for local islands with global ids ``gid``: (n_local, 6) records."""
+    gid = np.ascontiguousarray(gid, dtype=np.uint32)
+    rec = np.zeros((len(gid), REC_WORDS), dtype=np.uint32)
+    c = cfg._c()
+    lib().orc_emigrate(ctypes.byref(c), len(gid), _p(gid, ctypes.c_uint32),
+                       _p(np.ascontiguousarray(trait, dtype=np.uint32), ctypes.c_uint32),
+                       _p(np.ascontiguousarray(surf, dtype=np.uint64), ctypes.c_uint64),
+                       G, _p(rec, ctypes.c_uint32))
+    return rec
+
+
+def immigrate_select(cfg: Config, gid, nbr, active, trait, surf, rec, G: int):
+    """Steps a2-a6 for the active local islands; returns the children."""
+    gid = np.ascontiguousarray(gid, dtype=np.uint32)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    active = np.ascontiguousarray(active, dtype=np.uint8)
+    trait = np.ascontiguousarray(trait, dtype=np.uint32).copy()
+    surf = np.ascontiguousarray(surf, dtype=np.uint64).copy()
+    rec = np.ascontiguousarray(rec, dtype=np.uint32)
+    c = cfg._c()
+    if cfg.interval > 0 and G % cfg.interval == 0:
+        lib().orc_immigrate(ctypes.byref(c), len(gid), _p(gid, ctypes.c_uint32),
+                            _p(nbr, ctypes.c_int32), _vp(active),
+                            _p(trait, ctypes.c_uint32), _p(surf, ctypes.c_uint64),
+                            _p(rec, ctypes.c_uint32), G, None)
+    t2, s2 = trait.copy(), surf.copy()
+    lib().orc_select(ctypes.byref(c), len(gid), _p(gid, ctypes.c_uint32), _vp(active),
+                     _p(trait, ctypes.c_uint32), _p(surf, ctypes.c_uint64), None, G, G,
+                     _p(t2, ctypes.c_uint32), _p(s2, ctypes.c_uint64), None)
+    return t2, s2
+
+
+def neighbour(cfg: Config, island: int, d: int) -> int:
+    c = cfg._c()
+    return int(lib().orc_neighbour(ctypes.byref(c), island, d))

@@ -1,0 +1,487 @@
+/*
+ * hsga_oracle.c -- plain, slow, single-threaded CPU oracle for the
+ * tracking-enabled island-model genetic algorithm of Moreno, Yang, Dolson &
+ * Zaman, "Trackable Agent-based Evolution Models at Wafer Scale" (arXiv
+ * 2404.10861).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline / reference leg may load this library.  It shares
+ * no source, header, table or helper with the CUDA path; neither includes the
+ * other.
+ *
+ * What it computes, step by step, in the paper's order (section "Asynchronous
+ * Island-model Genetic Algorithm"): migration first, then fitness evaluation,
+ * tournament selection, mutation, and the hereditary-stratigraphy annotation
+ * update.  Synchronous-migration reading, with every random number drawn from
+ * a counter-based generator so that a run is a pure function of the seed:
+ *
+ *   a1 emigrate  : per island one emigrant slot and one direction (N,E,S,W)
+ *                  from Philox(key; 0xFFFFFFFF, island, G, 0); the genome is
+ *                  copied, not moved (emigration buffers are refilled with
+ *                  copies of random members).
+ *   a2 immigrate : for d = N,E,S,W in that order, an emigrant of the
+ *                  neighbour in direction d that targets this island replaces
+ *                  the member at slot floor(v_d * n / 2^32), with (v_0..v_3) =
+ *                  Philox(key; 0xFFFFFFFE, island, G, 0); later arrivals
+ *                  overwrite earlier ones.  All emigrants are chosen before any
+ *                  immigrant lands.
+ *   a3 evaluate  : fitness is the stored uint32 trait (the paper's trivial
+ *                  fitness function: the genome stores its own fitness).
+ *   a4 select    : child slot j draws its tournament from Philox(key; j,
+ *                  island, G, 1): candidates floor(w0*n/2^32),
+ *                  floor(w1*n/2^32) drawn with replacement; a later candidate
+ *                  replaces the current best only if strictly fitter.
+ *                  Candidates beyond the second come from purposes 2, 3, ...
+ *                  four per block.
+ *   a5 mutate    : w2 < floor(p_ben 2^32) -> trait + 1 (saturating);
+ *                  else w2 < floor(p_ben 2^32) + floor(p_del 2^32) -> trait - 1
+ *                  (saturating).
+ *   a6 deposit   : site = site_fn(policy, S, W, T); unless the policy discards
+ *                  this deposition, surface bits [site*b, site*b + b) take the
+ *                  low b bits of w3.  T, the deposition counter, is then one
+ *                  larger; in synchronous mode T equals the generation G.
+ *   a7 sample    : one genome per island at slot floor(w0*n/2^32) of
+ *                  Philox(key; 0xFFFFFFFD, island, G, 0), then k islands
+ *                  without replacement by a partial Fisher-Yates shuffle whose
+ *                  j-th draw is word 0 of Philox(key; j, 0xFFFFFFFF, G, 3).
+ *
+ * Random numbers: Philox4x32-10 of Salmon, Moraes, Dror & Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3" (SC'11), written here from that
+ * paper's definition.  The key is (seed_lo, seed_hi).  The same round and key
+ * schedule is instantiated at 64-bit words (Philox4x64-10) only so that a test
+ * can pin the round structure against numpy.random.Philox.
+ *
+ * Surface site selection: the paper leaves the indexing formulas to later
+ * work (section "Surface-based Hereditary Stratigraphy Algorithms"); it fixes
+ * only their properties: a fixed-size buffer written in place, implicit
+ * pruning by overwrite, timestamps recoverable from (site, T) alone, "steady"
+ * spreading retained time points evenly over history and "tilted" favouring
+ * recent ones.  The functions below are this project's own O(1) readings of
+ * those properties; the retention property tests pin them.  Parity with the
+ * paper's (unpublished here) site sequences is unpinned.
+ *
+ * Timestamp lookup is written as its definition: the last deposition time
+ * below T whose site is p, found by replaying the site function (brute force).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4xW-10 (Salmon et al. 2011, section 4): each round multiplies words
+ * 0 and 2 by the round multipliers, takes the high halves xor'd with words
+ * 1 and 3 and the round key, the low halves pass through; the key is bumped
+ * by the Weyl constants after every round.  One macro serves both widths so
+ * the 64-bit instance checks the structure of the 32-bit one. */
+#define ORC_PHILOX_DEFINE(NAME, UINT, WIDE, BITS, M0, M1, W0, W1)              \
+  void NAME(UINT k0, UINT k1, const UINT ctr[4], UINT out[4]) {               \
+    UINT c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];                  \
+    for (int round = 0; round < 10; ++round) {                                \
+      WIDE p0 = (WIDE)(M0) * (WIDE)c0;                                        \
+      WIDE p1 = (WIDE)(M1) * (WIDE)c2;                                        \
+      UINT hi0 = (UINT)(p0 >> BITS), lo0 = (UINT)p0;                          \
+      UINT hi1 = (UINT)(p1 >> BITS), lo1 = (UINT)p1;                          \
+      UINT n0 = hi1 ^ c1 ^ k0;                                                \
+      UINT n1 = lo1;                                                          \
+      UINT n2 = hi0 ^ c3 ^ k1;                                                \
+      UINT n3 = lo0;                                                          \
+      c0 = n0; c1 = n1; c2 = n2; c3 = n3;                                     \
+      k0 = (UINT)(k0 + (W0));                                                 \
+      k1 = (UINT)(k1 + (W1));                                                 \
+    }                                                                         \
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;                       \
+  }
+
+ORC_PHILOX_DEFINE(orc_philox4x32_10, uint32_t, uint64_t, 32,
+                  0xD2511F53u, 0xCD9E8D57u, 0x9E3779B9u, 0xBB67AE85u)
+ORC_PHILOX_DEFINE(orc_philox4x64_10, uint64_t, unsigned __int128, 64,
+                  0xD2E7470EE14C6C93ull, 0xCA5A826395121157ull,
+                  0x9E3779B97F4A7C15ull, 0xBB67AE8584CAA73Bull)
+
+/* floor(w * m / 2^32): a uniform index in [0, m) from one 32-bit word. */
+static uint32_t orc_index(uint32_t w, uint64_t m) {
+  return (uint32_t)(((uint64_t)w * m) >> 32);
+}
+
+static void orc_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                     uint32_t c3, uint32_t out[4]) {
+  uint32_t ctr[4] = {c0, c1, c2, c3};
+  orc_philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), ctr, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Surface site selection (readings; see header). */
+
+enum { ORC_STEADY = 0, ORC_TILTED = 1, ORC_STRETCHED = 2, ORC_TRIVIAL = 3,
+       ORC_NONE = 4 };
+
+static unsigned orc_bitlen(uint64_t x) {
+  unsigned n = 0;
+  while (x) { ++n; x >>= 1; }
+  return n;
+}
+
+static unsigned orc_ctz(uint64_t x) { /* x > 0 */
+  unsigned n = 0;
+  while (!(x & 1)) { ++n; x >>= 1; }
+  return n;
+}
+
+/* Returns the site in [0, S) written by deposition number T, or S when the
+ * policy discards that deposition.  S is a power of two; W divides S. */
+uint32_t orc_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T) {
+  if (policy == ORC_TRIVIAL) return (uint32_t)(T % S);
+  if (policy == ORC_STEADY) {
+    /* Epoch e: zero while the first S depositions fill the buffer, then
+     * bitlen(T) - log2(S).  Deposition T is kept only if 2^e divides T+1;
+     * writing T+1 = m*2^e (1 <= m <= S), its site is (T+1 mod S+1) - 1, a
+     * bijection of m because 2 is invertible modulo the odd S+1.  Each new
+     * epoch overwrites exactly the odd-m survivors of the previous one, so
+     * the kept times are the multiples of 2^e: evenly spread. */
+    unsigned s = orc_bitlen(S) - 1;
+    unsigned e = (T + 1 <= S) ? 0 : orc_bitlen(T) - s;
+    if (orc_ctz(T + 1) < e) return S;
+    return (uint32_t)((T + 1) % ((uint64_t)S + 1)) - 1;
+  }
+  if (policy == ORC_TILTED || policy == ORC_STRETCHED) {
+    /* Levels: deposition T belongs to level h = ctz(T+1) (capped at L-1,
+     * L = S/W), and is the j-th deposition of that level.  Tilted keeps the
+     * most recent W of every level in a per-level ring; stretched keeps the
+     * first W of every level. */
+    uint32_t L = S / W;
+    unsigned h = orc_ctz(T + 1);
+    uint32_t level;
+    uint64_t j;
+    if (h < L - 1) {
+      level = h;
+      j = (T + 1) >> (h + 1);
+    } else {
+      level = L - 1;
+      j = ((T + 1) >> (L - 1)) - 1;
+    }
+    if (policy == ORC_TILTED) return level * W + (uint32_t)(j % W);
+    return j < W ? level * W + (uint32_t)j : S;
+  }
+  return S; /* ORC_NONE: no surface */
+}
+
+/* Definition of the timestamp lookup: for every site, the largest deposition
+ * time t < T that wrote it, or -1 if none did.  Brute-force replay. */
+void orc_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
+                int64_t *times_out) {
+  for (uint32_t p = 0; p < S; ++p) times_out[p] = -1;
+  for (uint64_t t = 0; t < T; ++t) {
+    uint32_t site = orc_site(policy, S, W, t);
+    if (site < S) times_out[site] = (int64_t)t;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Genetic algorithm. */
+
+typedef struct orc_cfg {
+  uint32_t rows, cols, n, tournament;
+  uint32_t policy, bits, W, interval;
+  double p_ben, p_del;
+  uint64_t seed;
+} orc_cfg;
+
+enum { ORC_N = 0, ORC_E = 1, ORC_S = 2, ORC_W = 3 };
+
+/* Neighbour of global island g on the rows x cols torus in direction d. */
+uint32_t orc_neighbour(const orc_cfg *cfg, uint32_t g, uint32_t d) {
+  uint32_t r = g / cfg->cols, c = g % cfg->cols;
+  switch (d) {
+    case ORC_N: r = (r + cfg->rows - 1) % cfg->rows; break;
+    case ORC_S: r = (r + 1) % cfg->rows; break;
+    case ORC_E: c = (c + 1) % cfg->cols; break;
+    default:    c = (c + cfg->cols - 1) % cfg->cols; break;
+  }
+  return r * cfg->cols + c;
+}
+
+/* An emigrant record: the copied genome, its direction and, for pedigree
+ * tracking, the global agent index it was copied from. */
+#define ORC_REC_WORDS 6 /* trait, surf_lo, surf_hi, dir, src_lo, src_hi */
+
+/* a1: emigrant records of the local islands (global ids gid[0..n_local)).
+ * Population arrays are local: island l holds agents [l*n, l*n + n). */
+void orc_emigrate(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
+                  const uint32_t *trait, const uint64_t *surf, uint64_t G,
+                  uint32_t *rec) {
+  for (uint32_t l = 0; l < n_local; ++l) {
+    uint32_t w[4];
+    orc_draw(cfg->seed, 0xFFFFFFFFu, gid[l], (uint32_t)G, 0, w);
+    uint32_t slot = orc_index(w[0], cfg->n);
+    uint32_t dir = w[1] >> 30;
+    uint64_t src = (uint64_t)gid[l] * cfg->n + slot;
+    uint32_t *r = rec + (size_t)l * ORC_REC_WORDS;
+    r[0] = trait[(size_t)l * cfg->n + slot];
+    r[1] = (uint32_t)surf[(size_t)l * cfg->n + slot];
+    r[2] = (uint32_t)(surf[(size_t)l * cfg->n + slot] >> 32);
+    r[3] = dir;
+    r[4] = (uint32_t)src;
+    r[5] = (uint32_t)(src >> 32);
+  }
+}
+
+/* a2: in place on the active local islands.  nbr[l*4 + d] is the local index
+ * of the neighbour of l in direction d; its record is rec[that].  src (may be
+ * NULL) holds, per agent, the global agent index it descends from in the
+ * pre-migration population; immigrants overwrite it with theirs. */
+void orc_immigrate(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
+                   const int32_t *nbr, const uint8_t *active, uint32_t *trait,
+                   uint64_t *surf, const uint32_t *rec, uint64_t G,
+                   uint64_t *src) {
+  for (uint32_t l = 0; l < n_local; ++l) {
+    if (active && !active[l]) continue;
+    uint32_t v[4];
+    orc_draw(cfg->seed, 0xFFFFFFFEu, gid[l], (uint32_t)G, 0, v);
+    for (uint32_t d = 0; d < 4; ++d) {
+      int32_t nb = nbr[(size_t)l * 4 + d];
+      const uint32_t *r = rec + (size_t)nb * ORC_REC_WORDS;
+      uint32_t toward_me = (d + 2) % 4; /* the neighbour must aim back at l */
+      if (r[3] != toward_me) continue;
+      uint32_t slot = orc_index(v[d], cfg->n);
+      size_t a = (size_t)l * cfg->n + slot;
+      trait[a] = r[0];
+      surf[a] = (uint64_t)r[1] | ((uint64_t)r[2] << 32);
+      if (src) src[a] = (uint64_t)r[4] | ((uint64_t)r[5] << 32);
+    }
+  }
+}
+
+static uint64_t orc_threshold(double p) {
+  /* floor(p * 2^32); p in [0, 1]; multiplying by a power of two is exact. */
+  return (uint64_t)(p * 4294967296.0);
+}
+
+/* a3-a6 for the active local islands: parents (post-migration) in
+ * trait_in/surf_in, children to trait_out/surf_out.  T is the deposition
+ * counter the children's new differentia is stamped with.  parent_out (may
+ * be NULL) receives per child the pre-migration global agent index of its
+ * parent, using src (or the parent's own index when src is NULL). */
+void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
+                const uint8_t *active, const uint32_t *trait_in,
+                const uint64_t *surf_in, const uint64_t *src, uint64_t G,
+                uint64_t T, uint32_t *trait_out, uint64_t *surf_out,
+                uint64_t *parent_out) {
+  uint32_t n = cfg->n;
+  uint64_t thr_b = orc_threshold(cfg->p_ben);
+  uint64_t thr_d = orc_threshold(cfg->p_del);
+  uint32_t S = 64 / cfg->bits;
+  uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
+  uint64_t vmask = (cfg->bits == 64) ? ~0ull : ((1ull << cfg->bits) - 1);
+  for (uint32_t l = 0; l < n_local; ++l) {
+    if (active && !active[l]) continue;
+    const uint32_t *fit = trait_in + (size_t)l * n; /* a3: fitness = trait */
+    for (uint32_t j = 0; j < n; ++j) {
+      uint32_t w[4];
+      orc_draw(cfg->seed, j, gid[l], (uint32_t)G, 1, w);
+      /* a4: tournament of `tournament` candidates, with replacement. */
+      uint32_t best = orc_index(w[0], n);
+      for (uint32_t c = 1; c < cfg->tournament; ++c) {
+        uint32_t word;
+        if (c == 1) {
+          word = w[1];
+        } else {
+          uint32_t extra[4];
+          orc_draw(cfg->seed, j, gid[l], (uint32_t)G, 2 + (c - 2) / 4, extra);
+          word = extra[(c - 2) % 4];
+        }
+        uint32_t cand = orc_index(word, n);
+        if (fit[cand] > fit[best]) best = cand;
+      }
+      size_t pa = (size_t)l * n + best;
+      uint32_t trait = trait_in[pa];
+      uint64_t surface = surf_in[pa];
+      /* a5: mutation of the trait. */
+      if ((uint64_t)w[2] < thr_b) {
+        if (trait != 0xFFFFFFFFu) trait += 1;
+      } else if ((uint64_t)w[2] < thr_b + thr_d) {
+        if (trait != 0) trait -= 1;
+      }
+      /* a6: deposit the new differentia. */
+      if (cfg->policy != ORC_NONE && site < S) {
+        uint32_t shift = site * cfg->bits;
+        surface &= ~(vmask << shift);
+        surface |= ((uint64_t)w[3] & vmask) << shift;
+      }
+      size_t ca = (size_t)l * n + j;
+      trait_out[ca] = trait;
+      surf_out[ca] = surface;
+      if (parent_out)
+        parent_out[ca] = src ? src[pa] : (uint64_t)gid[l] * n + best;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Whole-torus driver. */
+
+static void orc_torus_tables(const orc_cfg *cfg, uint32_t *gid, int32_t *nbr) {
+  uint32_t I = cfg->rows * cfg->cols;
+  for (uint32_t g = 0; g < I; ++g) {
+    gid[g] = g;
+    for (uint32_t d = 0; d < 4; ++d)
+      nbr[(size_t)g * 4 + d] = (int32_t)orc_neighbour(cfg, g, d);
+  }
+}
+
+static int orc_migrates(const orc_cfg *cfg, uint64_t G) {
+  return cfg->interval > 0 && G % cfg->interval == 0;
+}
+
+/* Runs n_gens generations from generation G0 (sync mode: T = G).  When
+ * premigrated is nonzero the migration of generation G0 is taken as already
+ * done (see orc_migrate_grid).  parents (may be NULL) receives
+ * n_gens * rows*cols*n parent indices, generation-major.  Returns 0, or -1 on
+ * allocation failure. */
+int orc_run_grid(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
+                 uint64_t G0, uint64_t n_gens, int premigrated,
+                 uint64_t *parents) {
+  uint32_t I = cfg->rows * cfg->cols;
+  size_t A = (size_t)I * cfg->n;
+  uint32_t *gid = malloc(sizeof(uint32_t) * I);
+  int32_t *nbr = malloc(sizeof(int32_t) * I * 4);
+  uint32_t *rec = malloc(sizeof(uint32_t) * ORC_REC_WORDS * I);
+  uint32_t *t2 = malloc(sizeof(uint32_t) * A);
+  uint64_t *s2 = malloc(sizeof(uint64_t) * A);
+  uint64_t *src = parents ? malloc(sizeof(uint64_t) * A) : NULL;
+  if (!gid || !nbr || !rec || !t2 || !s2 || (parents && !src)) {
+    free(gid); free(nbr); free(rec); free(t2); free(s2); free(src);
+    return -1;
+  }
+  orc_torus_tables(cfg, gid, nbr);
+  for (uint64_t k = 0; k < n_gens; ++k) {
+    uint64_t G = G0 + k;
+    if (src)
+      for (size_t a = 0; a < A; ++a) src[a] = a;
+    if (orc_migrates(cfg, G) && !(premigrated && k == 0)) {
+      orc_emigrate(cfg, I, gid, trait, surf, G, rec);
+      orc_immigrate(cfg, I, gid, nbr, NULL, trait, surf, rec, G, src);
+    }
+    orc_select(cfg, I, gid, NULL, trait, surf, src, G, G, t2, s2,
+               parents ? parents + (size_t)k * A : NULL);
+    memcpy(trait, t2, sizeof(uint32_t) * A);
+    memcpy(surf, s2, sizeof(uint64_t) * A);
+  }
+  free(gid); free(nbr); free(rec); free(t2); free(s2); free(src);
+  return 0;
+}
+
+/* Explicit a1+a2 of generation G, in place, on the whole torus. */
+int orc_migrate_grid(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
+                     uint64_t G) {
+  uint32_t I = cfg->rows * cfg->cols;
+  uint32_t *gid = malloc(sizeof(uint32_t) * I);
+  int32_t *nbr = malloc(sizeof(int32_t) * I * 4);
+  uint32_t *rec = malloc(sizeof(uint32_t) * ORC_REC_WORDS * I);
+  if (!gid || !nbr || !rec) { free(gid); free(nbr); free(rec); return -1; }
+  orc_torus_tables(cfg, gid, nbr);
+  orc_emigrate(cfg, I, gid, trait, surf, G, rec);
+  orc_immigrate(cfg, I, gid, nbr, NULL, trait, surf, rec, G, NULL);
+  free(gid); free(nbr); free(rec);
+  return 0;
+}
+
+/* State at generation G0 + n_gens of one island (row r, column c) of a
+ * full-size torus, from a uniform founder state at G0 (every agent: trait0,
+ * surface0), computed on its dependency cone only: a (2n_gens+1)^2 box around
+ * the island; generation k advances the islands within Chebyshev radius
+ * n_gens-k-1 of the centre, whose four neighbours lie inside the radius-
+ * (n_gens-k) region known at that generation.  Requires 2*n_gens+1 <= rows
+ * and <= cols (no wrap-around onto itself).  Writes the island's n agents. */
+int orc_run_cone(const orc_cfg *cfg, uint32_t r, uint32_t c, uint32_t trait0,
+                 uint64_t surf0, uint64_t G0, uint32_t n_gens,
+                 uint32_t *trait_out, uint64_t *surf_out) {
+  uint32_t R = n_gens, D = 2 * R + 1, I = D * D, n = cfg->n;
+  if (D > cfg->rows || D > cfg->cols) return -2;
+  size_t A = (size_t)I * n;
+  uint32_t *gid = malloc(sizeof(uint32_t) * I);
+  int32_t *nbr = malloc(sizeof(int32_t) * I * 4);
+  uint8_t *active = malloc(I);
+  uint32_t *rec = malloc(sizeof(uint32_t) * ORC_REC_WORDS * I);
+  uint32_t *t1 = malloc(sizeof(uint32_t) * A), *t2 = malloc(sizeof(uint32_t) * A);
+  uint64_t *s1 = malloc(sizeof(uint64_t) * A), *s2 = malloc(sizeof(uint64_t) * A);
+  if (!gid || !nbr || !active || !rec || !t1 || !t2 || !s1 || !s2) {
+    free(gid); free(nbr); free(active); free(rec);
+    free(t1); free(t2); free(s1); free(s2);
+    return -1;
+  }
+  for (uint32_t y = 0; y < D; ++y)
+    for (uint32_t x = 0; x < D; ++x) {
+      uint32_t l = y * D + x;
+      uint32_t gr = (r + cfg->rows - R + y) % cfg->rows;
+      uint32_t gc = (c + cfg->cols - R + x) % cfg->cols;
+      gid[l] = gr * cfg->cols + gc;
+      nbr[l * 4 + ORC_N] = y > 0 ? (int32_t)(l - D) : -1;
+      nbr[l * 4 + ORC_S] = y + 1 < D ? (int32_t)(l + D) : -1;
+      nbr[l * 4 + ORC_E] = x + 1 < D ? (int32_t)(l + 1) : -1;
+      nbr[l * 4 + ORC_W] = x > 0 ? (int32_t)(l - 1) : -1;
+    }
+  for (size_t a = 0; a < A; ++a) { t1[a] = trait0; s1[a] = surf0; }
+  for (uint32_t k = 0; k < n_gens; ++k) {
+    uint64_t G = G0 + k;
+    uint32_t radius = R - k - 1;
+    for (uint32_t y = 0; y < D; ++y)
+      for (uint32_t x = 0; x < D; ++x) {
+        uint32_t dy = y > R ? y - R : R - y, dx = x > R ? x - R : R - x;
+        active[y * D + x] = (dy <= radius && dx <= radius);
+      }
+    memcpy(t2, t1, sizeof(uint32_t) * A);
+    memcpy(s2, s1, sizeof(uint64_t) * A);
+    if (orc_migrates(cfg, G)) {
+      /* Records of every island are computed; only those within the known
+       * region are read by the active islands. */
+      orc_emigrate(cfg, I, gid, t1, s1, G, rec);
+      orc_immigrate(cfg, I, gid, nbr, active, t1, s1, rec, G, NULL);
+    }
+    orc_select(cfg, I, gid, active, t1, s1, NULL, G, G, t2, s2, NULL);
+    uint32_t *tt = t1; t1 = t2; t2 = tt;
+    uint64_t *ss = s1; s1 = s2; s2 = ss;
+  }
+  size_t centre = (size_t)(R * D + R) * n;
+  memcpy(trait_out, t1 + centre, sizeof(uint32_t) * n);
+  memcpy(surf_out, s1 + centre, sizeof(uint64_t) * n);
+  free(gid); free(nbr); free(active); free(rec);
+  free(t1); free(t2); free(s1); free(s2);
+  return 0;
+}
+
+/* a7: sample k genomes at generation G (one candidate per island, then k
+ * distinct islands by partial Fisher-Yates).  out_words gets 4 words per
+ * sample (trait, surf_lo, surf_hi, T=G); out_island_slot (may be NULL) gets
+ * (island, slot).  Returns -2 if k exceeds the island count. */
+int orc_sample_grid(const orc_cfg *cfg, const uint32_t *trait,
+                    const uint64_t *surf, uint64_t G, uint32_t k,
+                    uint32_t *out_words, uint32_t *out_island_slot) {
+  uint32_t I = cfg->rows * cfg->cols;
+  if (k > I) return -2;
+  uint32_t *perm = malloc(sizeof(uint32_t) * (I ? I : 1));
+  if (!perm) return -1;
+  for (uint32_t i = 0; i < I; ++i) perm[i] = i;
+  for (uint32_t j = 0; j < k; ++j) {
+    uint32_t w[4];
+    orc_draw(cfg->seed, j, 0xFFFFFFFFu, (uint32_t)G, 3, w);
+    uint32_t pick = j + orc_index(w[0], I - j);
+    uint32_t tmp = perm[j]; perm[j] = perm[pick]; perm[pick] = tmp;
+  }
+  for (uint32_t j = 0; j < k; ++j) {
+    uint32_t island = perm[j];
+    uint32_t w[4];
+    orc_draw(cfg->seed, 0xFFFFFFFDu, island, (uint32_t)G, 0, w);
+    uint32_t slot = orc_index(w[0], cfg->n);
+    size_t a = (size_t)island * cfg->n + slot;
+    out_words[4 * j + 0] = trait[a];
+    out_words[4 * j + 1] = (uint32_t)surf[a];
+    out_words[4 * j + 2] = (uint32_t)(surf[a] >> 32);
+    out_words[4 * j + 3] = (uint32_t)G;
+    if (out_island_slot) {
+      out_island_slot[2 * j] = island;
+      out_island_slot[2 * j + 1] = slot;
+    }
+  }
+  free(perm);
+  return 0;
+}

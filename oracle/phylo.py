@@ -1,0 +1,251 @@
+"""Post-hoc phylogenetic analysis for the oracle: pedigree MRCA, surface MRCA
+bounds, trie reconstruction and phylometrics.
+
+TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``).
+
+Concepts from arXiv 2404.10861, section "Distributed Phylogenetic Tracking":
+every generation along a lineage appends one differentia; the first
+mismatching differentia between two genomes bounds their common ancestry
+from above, and a trie over the differentia sequences is the reconstruction.
+The trie here is this project's own simple version (the paper's
+agglomerative-trie algorithm lives in another paper):
+
+* all sampled genomes share the deposition count T (synchronous mode), so
+  they share the list of retained deposition times, given by the oracle's
+  timestamp lookup;
+* a genome is its differentiae in ascending deposition time; a trie node is
+  (time, value); the root sits at time -1 and leaves at time T;
+* unifurcations are collapsed; branch lengths are differences in time.
+
+Phylometrics (the on-hardware trial compares sum branch length and mean
+evolutionary distinctiveness between purifying-only and adaptive treatments):
+
+* sum branch length: total edge length;
+* mean pairwise distance: mean path length over leaf pairs;
+* Sackin: sum over leaves of the number of internal nodes on the root path;
+* Colless, generalised to polytomies: sum over internal nodes of
+  (largest - smallest child leaf count);
+* evolutionary distinctiveness (fair proportion): per leaf, the sum over the
+  edges on its root path of edge length / leaves below the edge.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import lookup
+
+
+# ------------------------------------------------------------ pedigree ---
+
+def lineage(parents: np.ndarray, agent: int) -> np.ndarray:
+    """Ancestor indices a_g for g = 0..G of ``agent`` at generation G
+    (a_G = agent; a_g = parents[g][a_{g+1}])."""
+    G = parents.shape[0]
+    out = np.zeros(G + 1, dtype=np.int64)
+    out[G] = agent
+    for g in range(G - 1, -1, -1):
+        out[g] = int(parents[g, out[g + 1]])
+    return out
+
+
+def true_mrca_generation(parents: np.ndarray, x: int, y: int) -> int:
+    """Largest g at which the lineages of x and y share one agent at the start
+    of generation g, or 0 when they never do (different founders).  Every
+    differentia deposited before that generation is shared; every one from it
+    on was drawn independently by each lineage."""
+    lx, ly = lineage(parents, x), lineage(parents, y)
+    same = np.nonzero(lx == ly)[0]
+    return int(same.max()) if len(same) else 0
+
+
+# ------------------------------------------------------------- surfaces ---
+
+def differentiae(surf: np.ndarray, bits: int) -> np.ndarray:
+    """(k, S) matrix of differentia values, site-major order."""
+    surf = np.asarray(surf, dtype=np.uint64).reshape(-1)
+    S = 64 // bits
+    shifts = (np.arange(S, dtype=np.uint64) * np.uint64(bits))
+    mask = np.uint64((1 << bits) - 1)
+    return ((surf[:, None] >> shifts[None, :]) & mask).astype(np.int64)
+
+
+def retained_order(policy: int, S: int, W: int, T: int):
+    """Sites holding a differentia after T depositions, in ascending
+    deposition time, and those times."""
+    times = lookup(policy, S, W, T)
+    sites = np.nonzero(times >= 0)[0]
+    order = sites[np.argsort(times[sites], kind="stable")]
+    return order, times[order]
+
+
+def mrca_bounds(da: np.ndarray, db: np.ndarray, times: np.ndarray):
+    """For two genomes' differentiae (already in time order) with deposition
+    times ``times``: (t_prev, t_star) where t_star is the first mismatching
+    retained time (None if all match) and t_prev the last retained time before
+    it (-1 if none).  Common ancestry ends at or before t_star."""
+    mism = np.nonzero(da != db)[0]
+    if len(mism) == 0:
+        return (int(times[-1]) if len(times) else -1), None
+    i = int(mism[0])
+    return (int(times[i - 1]) if i > 0 else -1), int(times[i])
+
+
+# ------------------------------------------------------- reconstruction ---
+
+class Tree:
+    """Rooted tree: parent index per node (-1 for the root), node times, and
+    which nodes are leaves (one per sampled genome, in sample order)."""
+
+    def __init__(self, parent, time, leaf_of_sample):
+        self.parent = np.asarray(parent, dtype=np.int64)
+        self.time = np.asarray(time, dtype=np.int64)
+        self.leaf_of_sample = np.asarray(leaf_of_sample, dtype=np.int64)
+
+    @property
+    def n_nodes(self):
+        return len(self.parent)
+
+    def children(self):
+        ch = [[] for _ in range(self.n_nodes)]
+        for v, p in enumerate(self.parent):
+            if p >= 0:
+                ch[p].append(v)
+        return ch
+
+
+def reconstruct(surf: np.ndarray, policy: int, bits: int, W: int, T: int) -> Tree:
+    """Trie reconstruction from sampled surfaces sharing deposition count T."""
+    S = 64 // bits
+    order, times = retained_order(policy, S, W, T)
+    D = differentiae(surf, bits)[:, order]
+    parent, time = [-1], [-1]
+    kids = [dict()]  # per node: value -> child node
+    leaf_of_sample = []
+    for row in D:
+        node = 0
+        for t, v in zip(times, row):
+            nxt = kids[node].get(int(v))
+            if nxt is None:
+                nxt = len(parent)
+                parent.append(node)
+                time.append(int(t))
+                kids.append(dict())
+                kids[node][int(v)] = nxt
+            node = nxt
+        leaf = len(parent)
+        parent.append(node)
+        time.append(int(T))
+        kids.append(dict())
+        leaf_of_sample.append(leaf)
+    return collapse(Tree(parent, time, leaf_of_sample))
+
+
+def collapse(tree: Tree) -> Tree:
+    """Remove internal non-root nodes with exactly one child (their edges
+    merge; total length is unchanged)."""
+    ch = tree.children()
+    leaves = set(int(x) for x in tree.leaf_of_sample)
+    keep = [v for v in range(tree.n_nodes)
+            if v == 0 or v in leaves or len(ch[v]) != 1]
+    new_id = {v: i for i, v in enumerate(keep)}
+
+    def kept_ancestor(v):
+        p = tree.parent[v]
+        while p != 0 and p not in new_id:
+            p = tree.parent[p]
+        return p
+
+    parent = [-1 if v == 0 else new_id[kept_ancestor(v)] for v in keep]
+    time = [int(tree.time[v]) for v in keep]
+    return Tree(parent, time, [new_id[int(x)] for x in tree.leaf_of_sample])
+
+
+# --------------------------------------------------------- phylometrics ---
+
+def _leaf_counts(tree: Tree):
+    ch = tree.children()
+    leaves = set(int(x) for x in tree.leaf_of_sample)
+    count = np.zeros(tree.n_nodes, dtype=np.int64)
+    # parents always precede children in construction order
+    for v in range(tree.n_nodes - 1, -1, -1):
+        count[v] += 1 if v in leaves else 0
+        if tree.parent[v] >= 0:
+            count[tree.parent[v]] += count[v]
+    return count, ch, leaves
+
+
+def sum_branch_length(tree: Tree) -> float:
+    p = tree.parent
+    m = p >= 0
+    return float((tree.time[m] - tree.time[p[m]]).sum())
+
+
+def mean_pairwise_distance(tree: Tree) -> float:
+    """Each edge lies on the path of every pair split by it:
+    sum = sum_edges length * k (N - k), over N (N - 1) / 2 pairs."""
+    count, _, _ = _leaf_counts(tree)
+    N = len(tree.leaf_of_sample)
+    if N < 2:
+        return 0.0
+    p = tree.parent
+    m = p >= 0
+    length = tree.time[m] - tree.time[p[m]]
+    k = count[m]
+    return float((length * k * (N - k)).sum() / (N * (N - 1) / 2))
+
+
+def pairwise_distance(tree: Tree, a: int, b: int) -> int:
+    """Path length between the leaves of samples a and b (brute force)."""
+    def path(v):
+        out = [v]
+        while tree.parent[out[-1]] >= 0:
+            out.append(int(tree.parent[out[-1]]))
+        return out
+    pa = path(int(tree.leaf_of_sample[a]))
+    pb = set(path(int(tree.leaf_of_sample[b])))
+    lca = next(v for v in pa if v in pb)
+    ta = tree.time[tree.leaf_of_sample[a]]
+    tb = tree.time[tree.leaf_of_sample[b]]
+    return int(ta + tb - 2 * tree.time[lca])
+
+
+def sackin(tree: Tree) -> int:
+    _, ch, leaves = _leaf_counts(tree)
+    total = 0
+    for leaf in tree.leaf_of_sample:
+        v = int(tree.parent[leaf])
+        while v >= 0:
+            total += 1
+            v = int(tree.parent[v])
+    return total
+
+
+def colless(tree: Tree) -> int:
+    count, ch, leaves = _leaf_counts(tree)
+    total = 0
+    for v in range(tree.n_nodes):
+        if ch[v]:
+            c = [int(count[u]) for u in ch[v]]
+            total += max(c) - min(c)
+    return total
+
+
+def evolutionary_distinctiveness(tree: Tree) -> np.ndarray:
+    count, _, _ = _leaf_counts(tree)
+    out = np.zeros(len(tree.leaf_of_sample))
+    for i, leaf in enumerate(tree.leaf_of_sample):
+        v = int(leaf)
+        while tree.parent[v] >= 0:
+            p = int(tree.parent[v])
+            out[i] += (tree.time[v] - tree.time[p]) / count[v]
+            v = p
+    return out
+
+
+def phylometrics(tree: Tree) -> dict:
+    ed = evolutionary_distinctiveness(tree)
+    return {"sum_branch_length": sum_branch_length(tree),
+            "mean_pairwise_distance": mean_pairwise_distance(tree),
+            "mean_evolutionary_distinctiveness": float(ed.mean()) if len(ed) else 0.0,
+            "sackin": sackin(tree),
+            "colless": colless(tree)}
