@@ -1,0 +1,351 @@
+"""Benchmark: agent replications per second of the island-model GA hot path
+(arXiv 2404.10861) on the wafer-shaped workload: 512 x 1024 toroidal islands
+x 32 agents = 16,777,216 agents, 3 x uint32 genomes (trait + 64-bit tilted
+surface of 1-bit differentiae), tournament 2, beneficial mutation 1e-3,
+synchronous migration every generation (the bit-exact mode).
+
+One step = GENS_PER_STEP generations of steps a1-a6 over the whole grid plus
+step a7 (10,000 sampled genomes).  Inputs live in HBM: the population is
+201 MB per plane, larger than the 129 MB L2, so no flush is needed between
+launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank runs an
+independent replica (its own seed): the island grid is replicated, not
+sharded, on this machine; timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ROWS, COLS, N_AGENTS = 512, 1024, 32
+GENS_PER_STEP = 100
+SAMPLE_K = 10000
+WORKLOAD = dict(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy="tilted", bits=1, W=2,
+                interval=1, p_ben=1e-3, p_del=0.0)
+AGENTS = ROWS * COLS * N_AGENTS
+# Algorithmic HBM bytes of one streamed generation launch: every agent's
+# 12-byte genome read once and its child's written once, plus one 12-byte
+# emigrant gather per island.
+BYTES_PER_LAUNCH = AGENTS * 24 + ROWS * COLS * 12
+
+
+def config_json(extra=None):
+    c = {"workload": "wafer-shaped island GA, sync migration (512x1024 islands x 32 agents)",
+         "islands": ROWS * COLS, "agents": AGENTS, "agents_per_island": N_AGENTS,
+         "genome": "3 x uint32 (trait + 64-bit tilted surface, 1-bit differentiae)",
+         "tournament": 2, "p_beneficial": 1e-3, "generations_per_step": GENS_PER_STEP,
+         "sample_per_step": SAMPLE_K, "kernel": "streamed",
+         "l2": "inputs larger than L2 (201 MB per population plane)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open(f"/tmp/hsga_clocks_{os.getpid()}.csv", "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.out:
+            self.out.close()
+
+    def summary(self):
+        path = f"/tmp/hsga_clocks_{os.getpid()}.csv"
+        try:
+            rows = [l.strip().split(", ") for l in open(path) if l.strip()]
+            os.unlink(path)
+        except Exception:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline_oracle(generations: int = 25):
+    """The oracle as it stands, single-threaded, on this host: the same
+    workload's first `generations` generations from founders."""
+    import oracle
+    oracle.build()
+    cfg = oracle.Config(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy=oracle.TILTED,
+                        bits=1, W=2, interval=1, p_ben=1e-3, seed=1)
+    t0 = time.perf_counter()
+    oracle.run(cfg, generations=generations)
+    dt = time.perf_counter() - t0
+    return {"value": AGENTS * generations / dt, "unit": "agent replications/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{generations} generations of the full 16.8M-agent grid from founders "
+                      f"({AGENTS * generations:.3g} replications, {dt:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cfg = oracle.Config(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy=oracle.TILTED,
+                        bits=1, W=2, interval=1, p_ben=1e-3, seed=1)
+    trait, surf = oracle.founders(cfg)
+    G = 0
+    # one step = one generation of the full grid (bounded CPU sample)
+    for _ in range(args.warmup):
+        trait, surf, _ = oracle.run(cfg, trait, surf, G0=G, generations=1)
+        G += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        trait, surf, _ = oracle.run(cfg, trait, surf, G0=G, generations=1)
+        G += 1
+    dt = time.perf_counter() - t0
+    value = AGENTS * args.steps / dt
+    line = {"impl": "reference", "metric": "agent replications/sec", "value": value,
+            "unit": "agent replications/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": config_json({"generations_per_step": 1, "sample_per_step": 0,
+                                   "kernel": "CPU oracle (plain C, single thread)"}),
+            "cpu_baseline": {"value": value, "unit": "agent replications/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} timed generations of the full grid"},
+            "e2e": {"value": value, "unit": "agent replications/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb
+    from paper_2404_10861_gb300 import inputs
+
+    _build.build()
+    rank, world, local = dist_setup(args.gpus)
+    hb.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    seed = 1 + rank
+    grid = hb.Grid(stream=stream.cuda_stream, kernel=hb.KERNEL_STREAMED, seed=seed, **WORKLOAD)
+    words = torch.zeros((SAMPLE_K, 4), dtype=torch.int32, device="cuda")
+    where = torch.zeros((SAMPLE_K, 2), dtype=torch.int32, device="cuda")
+
+    def step():
+        hb.hsga_run_generations(grid.handle, GENS_PER_STEP)
+        hb.hsga_sample_surfaces(grid.handle, SAMPLE_K, words, where)
+
+    for _ in range(args.warmup):
+        step()
+    hb.hsga_synchronize(grid.handle)
+    launches0 = grid.stats()["kernel_launches"]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            hb.hsga_run_generations(grid.handle, GENS_PER_STEP)
+            ev[i][1].record(stream)
+            hb.hsga_sample_surfaces(grid.handle, SAMPLE_K, words, where)
+            ev[i][2].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    hb.hsga_synchronize(grid.handle)
+    barrier(world)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    gen_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+    sample_ms = sum(b.elapsed_time(c) for _, b, c in ev)
+    launches = grid.stats()["kernel_launches"] - launches0
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    reps = AGENTS * GENS_PER_STEP * args.steps * world
+    value = reps / (elapsed_ms / 1e3)
+
+    # roofline of the dominant kernel (the streamed generation kernel)
+    per_launch_s = gen_ms / 1e3 / (GENS_PER_STEP * args.steps)
+    achieved = BYTES_PER_LAUNCH / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "step_streamed_wafer_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the C-ABI with host buffers: host->device population,
+    # generations, device->host sample, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        ht, hs = inputs.founders(AGENTS)
+        pin_t = torch.from_numpy(ht.view(np.int32)).pin_memory()
+        pin_s = torch.from_numpy(hs.view(np.int64)).pin_memory()
+        hw = np.zeros((SAMPLE_K, 4), dtype=np.uint32)
+        hwhere = np.zeros((SAMPLE_K, 2), dtype=np.uint32)
+        pin_w = torch.from_numpy(hw.view(np.int32)).pin_memory()
+        pin_where = torch.from_numpy(hwhere.view(np.int32)).pin_memory()
+        e2e_steps = args.e2e_steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            hb.hsga_set_population(grid.handle, pin_t, pin_s, 0)
+            hb.hsga_run_generations(grid.handle, GENS_PER_STEP)
+            hb.hsga_sample_surfaces(grid.handle, SAMPLE_K, pin_w, pin_where)
+        hb.hsga_synchronize(grid.handle)
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt, world)
+        e2e = {"value": AGENTS * GENS_PER_STEP * e2e_steps * world / dt,
+               "unit": "agent replications/s", "h2d_bytes_per_step": AGENTS * 12,
+               "d2h_bytes_per_step": SAMPLE_K * 24}
+    grid.close()
+
+    if rank == 0:
+        cpu = cpu_baseline_oracle() if (world == 1 and not args.no_cpu_baseline) else None
+        line = {"metric": "agent replications/sec", "value": value,
+                "unit": "agent replications/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic",
+                "config": config_json({"parallelism": f"replicas{world}"}),
+                "e2e": e2e,
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "step_streamed_kernel", "peak_kind": peak_kind,
+                             "algorithmic_bytes_per_launch": BYTES_PER_LAUNCH,
+                             "avg_launch_us": per_launch_s * 1e6},
+                "sample_ms_per_step": sample_ms / args.steps,
+                "clocks": clk.summary(),
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_profile(gens: int):
+    """Workload only, for profilers: founders, `gens` generations, one sample."""
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb
+    _build.build()
+    torch.cuda.set_device(0)
+    with hb.Grid(kernel=hb.KERNEL_STREAMED, seed=1, **WORKLOAD) as grid:
+        grid.run(gens)
+        grid.sample(SAMPLE_K)
+        grid.sync()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="steps of the end-to-end (host buffers) measurement")
+    ap.add_argument("--profile-gens", type=int, default=0,
+                    help="profiling mode: only run this many generations of the workload "
+                         "(no timing); used for ncu captures")
+    args = ap.parse_args()
+    if args.profile_gens:
+        run_profile(args.profile_gens)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

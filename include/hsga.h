@@ -1,0 +1,214 @@
+/*
+ * hsga.h -- C-ABI of the GB300 (sm_103a) hot path of the tracking-enabled
+ * island-model genetic algorithm of Moreno, Yang, Dolson & Zaman,
+ * "Trackable Agent-based Evolution Models at Wafer Scale" (arXiv 2404.10861).
+ *
+ * The library advances a rows x cols toroidal grid of islands, each holding
+ * n agents, one generation at a time.  Every generation follows the paper's
+ * cycle (section "Asynchronous Island-model Genetic Algorithm") in
+ * synchronous-migration form:
+ *   a1 emigrate   one random member of every island is copied toward a
+ *                 uniformly random von-Neumann neighbour;
+ *   a2 immigrate  arriving copies replace random members (directions N, E,
+ *                 S, W applied in that order);
+ *   a3 evaluate   fitness is the stored uint32 trait;
+ *   a4 select     tournament selection, ties to the first-drawn candidate;
+ *   a5 mutate     trait +1 with probability p_beneficial, else -1 with
+ *                 probability p_deleterious (both saturating);
+ *   a6 deposit    the hereditary-stratigraphy annotation update: a new
+ *                 random differentia of b bits is written into the 64-bit
+ *                 surface at the site the curation policy picks from
+ *                 (S, T) (sections "Distributed Phylogenetic Tracking" and
+ *                 "Surface-based Hereditary Stratigraphy Algorithms");
+ *   a7 sample     end-state genomes, one per island, then k islands without
+ *                 replacement (section "On-hardware Trial").
+ * All random numbers come from Philox4x32-10 keyed by the 64-bit seed, with
+ * counters (slot, island, generation, purpose), so a run is a pure function
+ * of its configuration.
+ *
+ * Conventions for every call:
+ *   - Return value: HSGA_OK (0) or a negative hsga_status; nothing is thrown
+ *     across the ABI.  hsga_status_string() names a status.
+ *   - Calls that touch the device are stream-ordered on the grid's stream and
+ *     asynchronous with respect to the host unless stated otherwise.
+ *   - Pointers marked "host or device" may be either; the library asks the
+ *     CUDA runtime which one it is and copies accordingly.  The caller owns
+ *     every buffer it passes; the library owns the grid and its buffers
+ *     until hsga_destroy().
+ *   - Genome record (the paper's 128-bit layout, section "Genome Model"):
+ *     4 x uint32 = [trait, surface bits 0..31, surface bits 32..63, T].
+ *     Differentia of site p occupies surface bits [p*b, p*b + b).
+ */
+#ifndef HSGA_H
+#define HSGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hsga_status {
+  HSGA_OK = 0,
+  HSGA_ERR_INVALID_ARG = -1,  /* a null pointer, a size or a field out of range */
+  HSGA_ERR_OOM = -2,          /* device allocation failed */
+  HSGA_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  HSGA_ERR_DEVICE = -4,       /* a kernel reported an inconsistent state */
+  HSGA_ERR_WAIT_TIMEOUT = -5, /* a bounded device-side wait ran out */
+  HSGA_ERR_UNSUPPORTED = -6   /* valid request this build cannot run */
+} hsga_status;
+
+/* Surface curation policies.  The paper defines steady (retained time points
+ * spread evenly over history) and tilted (recent time points preferred) and
+ * fixes their properties, not their formulas; this library's O(1) site
+ * functions are its own readings of those properties:
+ *   steady    epoch e = max(0, bitlen(T) - log2 S); keep T only when 2^e
+ *             divides T+1, at site ((T+1) mod (S+1)) - 1;
+ *   tilted    level h = min(ctz(T+1), L-1), L = S/W; a per-level ring keeps
+ *             the last W depositions of every level;
+ *   stretched same levels, keeps the first W depositions of every level;
+ *   trivial   site = T mod S (the paper's benchmark control);
+ *   none      no surface (the paper's untracked 32-bit genome). */
+typedef enum hsga_policy {
+  HSGA_STEADY = 0,
+  HSGA_TILTED = 1,
+  HSGA_STRETCHED = 2,
+  HSGA_TRIVIAL = 3,
+  HSGA_NONE = 4
+} hsga_policy;
+
+/* Which kernel advances generations. */
+typedef enum hsga_kernel {
+  HSGA_KERNEL_AUTO = 0,      /* resident when the grid fits on chip, else streamed */
+  HSGA_KERNEL_STREAMED = 1,  /* one launch per generation, population in HBM */
+  HSGA_KERNEL_RESIDENT = 2   /* persistent cooperative launch, genomes in registers */
+} hsga_kernel;
+
+/* Run configuration (plain data, caller-owned; copied by hsga_init_grid). */
+typedef struct hsga_config {
+  uint32_t rows, cols;          /* toroidal island grid, each >= 1 */
+  uint32_t agents_per_island;   /* n, 1..64 (the paper's runs use 32) */
+  uint32_t tournament_size;     /* 1..64 (the paper uses 5) */
+  uint32_t surface_policy;      /* hsga_policy */
+  uint32_t differentia_bits;    /* b in {1,2,4,8}; S = 64 / b sites */
+  uint32_t sites_per_level;     /* W for tilted / stretched: 1, 2 or 4, S/W >= 2 */
+  uint32_t migration_interval;  /* migrate when G % interval == 0; 0 = never */
+  double p_beneficial;          /* in [0,1]; p_beneficial + p_deleterious <= 1 */
+  double p_deleterious;
+  uint64_t seed;                /* Philox key (low word, high word) */
+  uint32_t kernel;              /* hsga_kernel */
+  uint32_t reserved;            /* must be 0 */
+} hsga_config;
+
+typedef struct hsga_stats {
+  uint64_t generation;          /* G: generations elapsed (= deposition count T) */
+  uint64_t replications;        /* agents x generations advanced by this grid */
+  uint64_t kernel_launches;     /* kernels this grid launched */
+  uint32_t kernel;              /* hsga_kernel that advances generations */
+  uint32_t islands_per_warp;    /* resident kernel tile shape (0 if streamed) */
+  uint32_t warps_per_block;
+  uint32_t blocks;
+} hsga_stats;
+
+typedef struct hsga_grid hsga_grid;
+
+/* Device allocator hooks (optional).  alloc returns device memory of at
+ * least `bytes` bytes usable on `stream`, or NULL; free releases it.  Set
+ * before hsga_init_grid; grids keep the hooks they were created with.
+ * Passing NULL for both restores the default (cudaMallocAsync/cudaFreeAsync
+ * on the grid's stream). */
+typedef void *(*hsga_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*hsga_free_fn)(void *ptr, void *stream, void *ctx);
+int hsga_set_allocator(hsga_alloc_fn alloc, hsga_free_fn free_fn, void *ctx);
+
+/* Creates a grid at generation 0 holding the founding population (every
+ * trait 0, every surface empty) on the current CUDA device.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Paper: the generational cycle and its startup (section "Asynchronous
+ * Island-model Genetic Algorithm"). */
+int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out);
+
+/* Replaces the population and sets the generation counter.
+ * trait: rows*cols*n uint32 (host or device); surf: rows*cols*n uint64
+ * (host or device); agent a of island i is entry i*n + a.
+ * generation: the new G (< 2^32 - 1).  A pending explicit migration is
+ * cleared.  Host buffers may be reused when the call returns. */
+int hsga_set_population(hsga_grid *g, const uint32_t *trait,
+                        const uint64_t *surf, uint64_t generation);
+
+/* Copies the population out (same layout as hsga_set_population; host or
+ * device).  Synchronous when either destination is host memory. */
+int hsga_get_population(hsga_grid *g, uint32_t *trait, uint64_t *surf);
+
+/* Advances n_generations full cycles (steps a1-a6 each).
+ * Paper: the main update loop repeated to a generation-count halt. */
+int hsga_run_generations(hsga_grid *g, uint64_t n_generations);
+
+/* Applies steps a1+a2 (emigrate, immigrate) of the current generation now,
+ * in place; the next hsga_run_generations skips that generation's migration.
+ * A second call before advancing returns HSGA_ERR_INVALID_ARG.
+ * Paper: migration is handled first in every cycle. */
+int hsga_migrate(hsga_grid *g);
+
+/* Step a7: k end-state genomes.  Each island offers the member at slot
+ * floor(w0*n/2^32) of Philox(seed; 0xFFFFFFFD, island, G, 0); k distinct
+ * islands are chosen by a partial Fisher-Yates shuffle whose j-th draw is
+ * word 0 of Philox(seed; j, 0xFFFFFFFF, G, 3).
+ * out_words: k*4 uint32 genome records (host or device);
+ * out_island_slot: k*2 uint32 (island, slot) or NULL (host or device).
+ * k = 0 is a no-op; k > rows*cols is HSGA_ERR_INVALID_ARG.  Synchronous when
+ * an output is host memory.
+ * Paper: one genome sampled per PE, then subsamples of 10k (section
+ * "On-hardware Trial"). */
+int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
+                         uint32_t *out_island_slot);
+
+/* Waits for the grid's stream and returns the first error a kernel reported
+ * (HSGA_ERR_WAIT_TIMEOUT, HSGA_ERR_DEVICE) or a pending CUDA error. */
+int hsga_synchronize(hsga_grid *g);
+
+/* Host-side counters (no device access). */
+int hsga_get_stats(const hsga_grid *g, hsga_stats *out);
+
+/* Checkpoint.  hsga_save with buf == NULL stores the required size in *len;
+ * otherwise writes config, generation and population into buf (host memory,
+ * *len bytes available) and stores the bytes written.  hsga_load restores a
+ * checkpoint taken from a grid of identical configuration; continuing from it
+ * is bit-identical to an uninterrupted run.  Both are synchronous. */
+int hsga_save(hsga_grid *g, void *buf, size_t *len);
+int hsga_load(hsga_grid *g, const void *buf, size_t len);
+
+/* Frees the grid and its device buffers (after waiting for its stream). */
+void hsga_destroy(hsga_grid *g);
+
+/* Site written by deposition number T (T < 2^32 - 1) under `policy` with S
+ * sites (power of two, 8..64) and W sites per level; returns S when the
+ * policy discards that deposition.  Host function. */
+uint32_t hsga_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T);
+
+/* Timestamp lookup: deposition time held by every site after T depositions,
+ * from (site, T) alone (section "Distributed Phylogenetic Tracking": no
+ * stored timestamps).  times_out: S int64 (host), -1 for a site never
+ * written.  Closed form, O(S).  Host function. */
+int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
+                int64_t *times_out);
+
+/* Site function on the device for T = T0 .. T0+count-1 (T0+count < 2^32):
+ * out_dev[i] = hsga_site(policy, S, W, T0 + i).  out_dev: device uint32.
+ * Stream-ordered on cuda_stream.  The paper's per-operation surface
+ * microbenchmark (section "Surface Algorithm Benchmark on Conventional
+ * CPU"). */
+int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
+                      uint64_t count, uint32_t *out_dev, void *cuda_stream);
+
+const char *hsga_status_string(int status);
+
+/* ABI version (major * 100 + minor). */
+int hsga_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSGA_H */

@@ -1,0 +1,295 @@
+"""ctypes binding of ``libhsga.so`` (C-ABI declared in ``include/hsga.h``).
+
+Argument marshalling only: every step of the generation cycle runs in the
+library's CUDA kernels.  The functions keep the C names.  Arrays may be numpy
+arrays (host memory) or CUDA torch tensors (device memory); the library tells
+them apart.  The library must exist (``__graft_entry__.build()`` or
+``python -m paper_2404_10861_gb300._build``); importing a missing or stale
+library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+STEADY, TILTED, STRETCHED, TRIVIAL, NONE = 0, 1, 2, 3, 4
+POLICIES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
+            "trivial": TRIVIAL, "none": NONE}
+KERNEL_AUTO, KERNEL_STREAMED, KERNEL_RESIDENT = 0, 1, 2
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed",
+          -3: "CUDA runtime error", -4: "kernel reported an inconsistent state",
+          -5: "bounded device wait timed out", -6: "unsupported"}
+
+
+class HsgaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class hsga_config(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint32), ("cols", ctypes.c_uint32),
+                ("agents_per_island", ctypes.c_uint32), ("tournament_size", ctypes.c_uint32),
+                ("surface_policy", ctypes.c_uint32), ("differentia_bits", ctypes.c_uint32),
+                ("sites_per_level", ctypes.c_uint32), ("migration_interval", ctypes.c_uint32),
+                ("p_beneficial", ctypes.c_double), ("p_deleterious", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class hsga_stats(ctypes.Structure):
+    _fields_ = [("generation", ctypes.c_uint64), ("replications", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
+                ("islands_per_warp", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+# Every symbol include/hsga.h declares, with its ctypes signature.
+_SIGS = {
+    "hsga_version": ([], ctypes.c_int),
+    "hsga_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "hsga_set_allocator": ([ALLOC_FN, FREE_FN, ctypes.c_void_p], ctypes.c_int),
+    "hsga_init_grid": ([ctypes.POINTER(hsga_config), ctypes.c_void_p,
+                        ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "hsga_set_population": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_uint64], ctypes.c_int),
+    "hsga_get_population": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hsga_run_generations": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "hsga_migrate": ([ctypes.c_void_p], ctypes.c_int),
+    "hsga_sample_surfaces": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                              ctypes.c_void_p], ctypes.c_int),
+    "hsga_synchronize": ([ctypes.c_void_p], ctypes.c_int),
+    "hsga_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_stats)], ctypes.c_int),
+    "hsga_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+                  ctypes.c_int),
+    "hsga_load": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "hsga_destroy": ([ctypes.c_void_p], None),
+    "hsga_site": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64],
+                  ctypes.c_uint32),
+    "hsga_lookup": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                     ctypes.c_void_p], ctypes.c_int),
+    "hsga_sites_device": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libhsga.so, raising if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (argt, rest) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = argt
+            fn.restype = rest
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise HsgaError(status, what)
+
+
+def _ptr(a):
+    """Raw address of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported buffer {type(a)}")
+
+
+# ------------------------------------------------------------- allocator ---
+_alloc_keep = []
+
+
+def use_torch_allocator():
+    """Routes the library's device allocations through torch's caching
+    allocator (PyTorch provides device memory and streams)."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _alloc_keep.append(cbs)
+    _check(lib().hsga_set_allocator(cbs[0], cbs[1], None), "hsga_set_allocator")
+
+
+def use_default_allocator():
+    _check(lib().hsga_set_allocator(ALLOC_FN(), FREE_FN(), None), "hsga_set_allocator")
+
+
+# ------------------------------------------------------------ functions ---
+def make_config(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2,
+                interval=1, p_ben=0.0, p_del=0.0, seed=1, kernel=KERNEL_AUTO) -> hsga_config:
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    return hsga_config(rows, cols, n, tournament, pol, bits, W, interval, p_ben, p_del,
+                       seed, kernel, 0)
+
+
+def hsga_init_grid(cfg: hsga_config, cuda_stream=None) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+    _check(lib().hsga_init_grid(ctypes.byref(cfg), stream, ctypes.byref(out)), "hsga_init_grid")
+    return out
+
+
+def hsga_set_population(g, trait, surf, generation: int):
+    _check(lib().hsga_set_population(g, _ptr(trait), _ptr(surf), int(generation)),
+           "hsga_set_population")
+
+
+def hsga_get_population(g, trait, surf):
+    _check(lib().hsga_get_population(g, _ptr(trait), _ptr(surf)), "hsga_get_population")
+
+
+def hsga_run_generations(g, n: int):
+    _check(lib().hsga_run_generations(g, int(n)), "hsga_run_generations")
+
+
+def hsga_migrate(g):
+    _check(lib().hsga_migrate(g), "hsga_migrate")
+
+
+def hsga_sample_surfaces(g, k: int, out_words, out_island_slot=None):
+    _check(lib().hsga_sample_surfaces(g, int(k), _ptr(out_words), _ptr(out_island_slot)),
+           "hsga_sample_surfaces")
+
+
+def hsga_synchronize(g):
+    _check(lib().hsga_synchronize(g), "hsga_synchronize")
+
+
+def hsga_get_stats(g) -> dict:
+    st = hsga_stats()
+    _check(lib().hsga_get_stats(g, ctypes.byref(st)), "hsga_get_stats")
+    return {f: getattr(st, f) for f, _ in hsga_stats._fields_}
+
+
+def hsga_save(g) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().hsga_save(g, None, ctypes.byref(n)), "hsga_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().hsga_save(g, buf, ctypes.byref(n)), "hsga_save")
+    return buf.raw[:n.value]
+
+
+def hsga_load(g, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().hsga_load(g, buf, len(blob)), "hsga_load")
+
+
+def hsga_destroy(g):
+    if g:
+        lib().hsga_destroy(g)
+
+
+def hsga_site(policy: int, S: int, W: int, T: int) -> int:
+    return int(lib().hsga_site(policy, S, W, T))
+
+
+def hsga_lookup(policy: int, S: int, W: int, T: int) -> np.ndarray:
+    out = np.zeros(S, dtype=np.int64)
+    _check(lib().hsga_lookup(policy, S, W, T, _ptr(out)), "hsga_lookup")
+    return out
+
+
+def hsga_sites_device(policy: int, S: int, W: int, T0: int, count: int, out_dev, stream=None):
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().hsga_sites_device(policy, S, W, T0, count, _ptr(out_dev), s),
+           "hsga_sites_device")
+
+
+# ----------------------------------------------------------- convenience ---
+@dataclass
+class Grid:
+    """Owning wrapper: ``Grid(**config)``; methods call the C-ABI above."""
+
+    def __init__(self, stream=None, **kw):
+        self.cfg = make_config(**kw)
+        self.handle = hsga_init_grid(self.cfg, stream)
+
+    @property
+    def agents(self) -> int:
+        return self.cfg.rows * self.cfg.cols * self.cfg.agents_per_island
+
+    @property
+    def islands(self) -> int:
+        return self.cfg.rows * self.cfg.cols
+
+    def set_population(self, trait, surf, generation):
+        hsga_set_population(self.handle, trait, surf, generation)
+
+    def population(self):
+        t = np.zeros(self.agents, dtype=np.uint32)
+        s = np.zeros(self.agents, dtype=np.uint64)
+        hsga_get_population(self.handle, t, s)
+        return t, s
+
+    def run(self, n):
+        hsga_run_generations(self.handle, n)
+
+    def migrate(self):
+        hsga_migrate(self.handle)
+
+    def sample(self, k):
+        w = np.zeros((k, 4), dtype=np.uint32)
+        where = np.zeros((k, 2), dtype=np.uint32)
+        hsga_sample_surfaces(self.handle, k, w, where)
+        return w, where
+
+    def sync(self):
+        hsga_synchronize(self.handle)
+
+    def stats(self):
+        return hsga_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            hsga_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,532 @@
+// hsga_capi.cu -- C-ABI runtime: grid lifetime, device memory, dispatch of
+// the generation kernels, checkpointing, and the host-side site / lookup
+// functions.  Declarations and contracts: include/hsga.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "hsga.h"
+#include "hsga_internal.h"
+
+using namespace hsga;
+
+namespace {
+
+struct Allocator {
+  hsga_alloc_fn alloc = nullptr;
+  hsga_free_fn free_fn = nullptr;
+  void *ctx = nullptr;
+};
+Allocator g_allocator;
+
+constexpr uint64_t kCheckpointMagic = 0x3130485341475348ull;  // "HSGAH01"
+constexpr uint64_t kMaxGeneration = 0xFFFFFFFFull - 64;        // Philox counter word
+
+}  // namespace
+
+struct hsga_grid {
+  hsga_config cfg;
+  RunParams p;
+  Allocator alloc;
+  cudaStream_t stream = nullptr;
+  uint64_t agents = 0;
+  uint32_t *trait[2] = {nullptr, nullptr};
+  uint64_t *surf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint4 *rec = nullptr;      // 2 x islands migrant records
+  uint32_t *flags = nullptr; // islands
+  int *err = nullptr;        // device error word
+  uint32_t *sample_scratch = nullptr;
+  size_t sample_scratch_bytes = 0;
+  uint64_t G = 0;
+  bool premigrated = false;
+  bool resident = false;
+  ResidentPlan plan;
+  bool broken = false;
+  uint64_t replications = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(const Allocator &a, void *ptr, cudaStream_t s) {
+  if (!ptr) return;
+  if (a.free_fn) a.free_fn(ptr, (void *)s, a.ctx);
+  else cudaFreeAsync(ptr, s);
+}
+
+bool is_device_ptr(const void *ptr) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? HSGA_OK : HSGA_ERR_CUDA; }
+
+bool power_of_two(uint32_t x) { return x && !(x & (x - 1)); }
+
+int validate(const hsga_config *c) {
+  if (!c) return HSGA_ERR_INVALID_ARG;
+  if (c->rows == 0 || c->cols == 0) return HSGA_ERR_INVALID_ARG;
+  if ((uint64_t)c->rows * c->cols >= 0xFFFFFFF0ull) return HSGA_ERR_INVALID_ARG;
+  if (c->agents_per_island == 0 || c->agents_per_island > 64) return HSGA_ERR_INVALID_ARG;
+  if (c->tournament_size == 0 || c->tournament_size > 64) return HSGA_ERR_INVALID_ARG;
+  if (c->surface_policy > HSGA_NONE) return HSGA_ERR_INVALID_ARG;
+  const uint32_t b = c->differentia_bits;
+  if (!(b == 1 || b == 2 || b == 4 || b == 8)) return HSGA_ERR_INVALID_ARG;
+  const uint32_t S = 64 / b, W = c->sites_per_level;
+  if (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED) {
+    if (!(W == 1 || W == 2 || W == 4) || S / W < 2) return HSGA_ERR_INVALID_ARG;
+  }
+  if (!(c->p_beneficial >= 0.0 && c->p_beneficial <= 1.0)) return HSGA_ERR_INVALID_ARG;
+  if (!(c->p_deleterious >= 0.0 && c->p_deleterious <= 1.0)) return HSGA_ERR_INVALID_ARG;
+  if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
+  if (c->kernel > HSGA_KERNEL_RESIDENT || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
+  return HSGA_OK;
+}
+
+uint64_t threshold(double p) { return (uint64_t)(p * 4294967296.0); }
+
+RunParams make_params(const hsga_config *c) {
+  RunParams p{};
+  p.rows = c->rows;
+  p.cols = c->cols;
+  p.n = c->agents_per_island;
+  p.islands = c->rows * c->cols;
+  p.tournament = c->tournament_size;
+  p.k0 = (uint32_t)c->seed;
+  p.k1 = (uint32_t)(c->seed >> 32);
+  p.policy = c->surface_policy;
+  p.bits = c->differentia_bits;
+  p.S = 64 / p.bits;
+  p.W = (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED)
+            ? c->sites_per_level
+            : 2;
+  p.interval = c->migration_interval;
+  p.thr_ben = threshold(c->p_beneficial);
+  p.thr_bd = p.thr_ben + threshold(c->p_deleterious);
+  p.vmask = (1ull << p.bits) - 1;
+  return p;
+}
+
+int fetch_device_error(hsga_grid *g) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  if (h == kDevErrWaitTimeout) {
+    g->broken = true;
+    return HSGA_ERR_WAIT_TIMEOUT;
+  }
+  if (h != 0) {
+    g->broken = true;
+    return HSGA_ERR_DEVICE;
+  }
+  return HSGA_OK;
+}
+
+void free_grid(hsga_grid *g) {
+  if (!g) return;
+  for (int i = 0; i < 2; ++i) {
+    dev_free(g->alloc, g->trait[i], g->stream);
+    dev_free(g->alloc, g->surf[i], g->stream);
+  }
+  dev_free(g->alloc, g->rec, g->stream);
+  dev_free(g->alloc, g->flags, g->stream);
+  dev_free(g->alloc, g->err, g->stream);
+  dev_free(g->alloc, g->sample_scratch, g->stream);
+  cudaStreamSynchronize(g->stream);
+  delete g;
+}
+
+// Copy count elements of `bytes_each` between host/device `src` and device `dst`.
+cudaError_t copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+}
+
+int reset_sync_state(hsga_grid *g) {
+  cudaError_t e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), g->stream);
+  g->broken = false;
+  g->premigrated = false;
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hsga_version(void) { return 100; }
+
+const char *hsga_status_string(int s) {
+  switch (s) {
+    case HSGA_OK: return "ok";
+    case HSGA_ERR_INVALID_ARG: return "invalid argument";
+    case HSGA_ERR_OOM: return "device allocation failed";
+    case HSGA_ERR_CUDA: return "CUDA runtime error";
+    case HSGA_ERR_DEVICE: return "kernel reported an inconsistent state";
+    case HSGA_ERR_WAIT_TIMEOUT: return "bounded device wait timed out";
+    case HSGA_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int hsga_set_allocator(hsga_alloc_fn alloc, hsga_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return HSGA_ERR_INVALID_ARG;
+  g_allocator.alloc = alloc;
+  g_allocator.free_fn = free_fn;
+  g_allocator.ctx = ctx;
+  return HSGA_OK;
+}
+
+int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
+  if (!out) return HSGA_ERR_INVALID_ARG;
+  *out = nullptr;
+  int v = validate(cfg);
+  if (v != HSGA_OK) return v;
+  hsga_grid *g = new (std::nothrow) hsga_grid();
+  if (!g) return HSGA_ERR_OOM;
+  g->cfg = *cfg;
+  g->p = make_params(cfg);
+  g->alloc = g_allocator;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->agents = (uint64_t)g->p.islands * g->p.n;
+  const bool tracked = cfg->surface_policy != HSGA_NONE;
+  for (int i = 0; i < 2; ++i) {
+    g->trait[i] = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->agents, g->stream);
+    g->surf[i] = tracked ? (uint64_t *)dev_alloc(g->alloc, sizeof(uint64_t) * g->agents, g->stream)
+                         : nullptr;
+  }
+  g->rec = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
+  g->flags = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->p.islands, g->stream);
+  g->err = (int *)dev_alloc(g->alloc, sizeof(int), g->stream);
+  bool ok = g->trait[0] && g->trait[1] && g->rec && g->flags && g->err &&
+            (!tracked || (g->surf[0] && g->surf[1]));
+  if (!ok) {
+    free_grid(g);
+    return HSGA_ERR_OOM;
+  }
+  cudaError_t e = cudaMemsetAsync(g->trait[0], 0, sizeof(uint32_t) * g->agents, g->stream);
+  if (e == cudaSuccess && tracked)
+    e = cudaMemsetAsync(g->surf[0], 0, sizeof(uint64_t) * g->agents, g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
+  if (e != cudaSuccess || reset_sync_state(g) != HSGA_OK) {
+    free_grid(g);
+    return HSGA_ERR_CUDA;
+  }
+  g->resident = false;
+  if (cfg->kernel != HSGA_KERNEL_STREAMED) {
+    g->resident = resident_plan(g->p, &g->plan);
+    if (!g->resident && cfg->kernel == HSGA_KERNEL_RESIDENT) {
+      free_grid(g);
+      return HSGA_ERR_UNSUPPORTED;
+    }
+  }
+  *out = g;
+  return HSGA_OK;
+}
+
+int hsga_set_population(hsga_grid *g, const uint32_t *trait, const uint64_t *surf,
+                        uint64_t generation) {
+  if (!g || !trait || generation > kMaxGeneration) return HSGA_ERR_INVALID_ARG;
+  const bool tracked = g->surf[0] != nullptr;
+  if (tracked && !surf) return HSGA_ERR_INVALID_ARG;
+  g->cur = 0;
+  cudaError_t e = copy_in(g->trait[0], trait, sizeof(uint32_t) * g->agents, g->stream);
+  if (e == cudaSuccess && tracked)
+    e = copy_in(g->surf[0], surf, sizeof(uint64_t) * g->agents, g->stream);
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  g->G = generation;
+  int r = reset_sync_state(g);
+  if (r != HSGA_OK) return r;
+  // host sources may be reused on return
+  if (!is_device_ptr(trait) || (tracked && !is_device_ptr(surf)))
+    return cuda_status(cudaStreamSynchronize(g->stream));
+  return HSGA_OK;
+}
+
+int hsga_get_population(hsga_grid *g, uint32_t *trait, uint64_t *surf) {
+  if (!g || !trait) return HSGA_ERR_INVALID_ARG;
+  const bool tracked = g->surf[0] != nullptr;
+  cudaError_t e = cudaMemcpyAsync(trait, g->trait[g->cur], sizeof(uint32_t) * g->agents,
+                                  cudaMemcpyDefault, g->stream);
+  if (e == cudaSuccess && surf) {
+    if (tracked)
+      e = cudaMemcpyAsync(surf, g->surf[g->cur], sizeof(uint64_t) * g->agents, cudaMemcpyDefault,
+                          g->stream);
+    else
+      e = is_device_ptr(surf) ? cudaMemsetAsync(surf, 0, sizeof(uint64_t) * g->agents, g->stream)
+                              : (memset(surf, 0, sizeof(uint64_t) * g->agents), cudaSuccess);
+  }
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  if (!is_device_ptr(trait) || (surf && !is_device_ptr(surf)))
+    return cuda_status(cudaStreamSynchronize(g->stream));
+  return HSGA_OK;
+}
+
+int hsga_run_generations(hsga_grid *g, uint64_t n) {
+  if (!g) return HSGA_ERR_INVALID_ARG;
+  if (g->broken) return HSGA_ERR_DEVICE;
+  if (n == 0) return HSGA_OK;
+  if (g->G + n > kMaxGeneration) return HSGA_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  if (g->resident) {
+    // Launch in slices so a single launch stays short.
+    const uint64_t slice = 1u << 16;
+    uint64_t done = 0;
+    while (done < n && e == cudaSuccess) {
+      const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
+      e = launch_step_resident(g->p, g->plan, (uint32_t)(g->G + done), m,
+                               g->premigrated && done == 0, g->trait[g->cur], g->surf[g->cur],
+                               g->rec, g->flags, g->err, g->stream);
+      g->launches++;
+      done += m;
+    }
+  } else {
+    for (uint64_t k = 0; k < n && e == cudaSuccess; ++k) {
+      const uint64_t G = g->G + k;
+      const bool do_mig = migrates(g->p, G) && !(g->premigrated && k == 0);
+      e = launch_step_streamed(g->p, (uint32_t)G, do_mig, g->trait[g->cur], g->surf[g->cur],
+                               g->trait[1 - g->cur], g->surf[1 - g->cur], g->stream);
+      g->cur = 1 - g->cur;
+      g->launches++;
+    }
+  }
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  g->G += n;
+  g->premigrated = false;
+  g->replications += n * g->agents;
+  return HSGA_OK;
+}
+
+int hsga_migrate(hsga_grid *g) {
+  if (!g) return HSGA_ERR_INVALID_ARG;
+  if (g->broken) return HSGA_ERR_DEVICE;
+  if (g->premigrated) return HSGA_ERR_INVALID_ARG;
+  cudaError_t e = launch_migrate(g->p, (uint32_t)g->G, g->trait[g->cur], g->surf[g->cur], g->rec,
+                                 g->stream);
+  g->launches += 2;
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  g->premigrated = true;
+  return HSGA_OK;
+}
+
+int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
+                         uint32_t *out_island_slot) {
+  if (!g || (k > 0 && !out_words)) return HSGA_ERR_INVALID_ARG;
+  if (k > g->p.islands) return HSGA_ERR_INVALID_ARG;
+  if (k == 0) return HSGA_OK;
+  const size_t scratch = sample_scratch_bytes(g->p, k);
+  if (scratch > g->sample_scratch_bytes) {
+    dev_free(g->alloc, g->sample_scratch, g->stream);
+    g->sample_scratch = (uint32_t *)dev_alloc(g->alloc, scratch, g->stream);
+    g->sample_scratch_bytes = g->sample_scratch ? scratch : 0;
+    if (!g->sample_scratch) return HSGA_ERR_OOM;
+  }
+  // the kernels store 16-byte records and 8-byte pairs: misaligned device
+  // outputs go through the staging buffer like host outputs
+  const bool dev_words = is_device_ptr(out_words) && ((uintptr_t)out_words % 16) == 0;
+  const bool dev_is = out_island_slot == nullptr ||
+                      (is_device_ptr(out_island_slot) && ((uintptr_t)out_island_slot % 8) == 0);
+  uint32_t *dw = out_words, *di = out_island_slot;
+  uint32_t *staging = nullptr;
+  if (!dev_words || !dev_is) {
+    staging = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * 6 * (size_t)k, g->stream);
+    if (!staging) return HSGA_ERR_OOM;
+    if (!dev_words) dw = staging;
+    if (!dev_is) di = staging + 4 * (size_t)k;
+  }
+  cudaError_t e = launch_sample(g->p, (uint32_t)g->G, k, g->trait[g->cur], g->surf[g->cur], dw,
+                                di, g->sample_scratch, g->stream);
+  g->launches++;
+  if (e == cudaSuccess && !dev_words)
+    e = cudaMemcpyAsync(out_words, dw, sizeof(uint32_t) * 4 * (size_t)k, cudaMemcpyDefault,
+                        g->stream);
+  if (e == cudaSuccess && !dev_is)
+    e = cudaMemcpyAsync(out_island_slot, di, sizeof(uint32_t) * 2 * (size_t)k, cudaMemcpyDefault,
+                        g->stream);
+  if (staging) {
+    dev_free(g->alloc, staging, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  }
+  return cuda_status(e);
+}
+
+int hsga_synchronize(hsga_grid *g) {
+  if (!g) return HSGA_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  return fetch_device_error(g);
+}
+
+int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
+  if (!g || !out) return HSGA_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->generation = g->G;
+  out->replications = g->replications;
+  out->kernel_launches = g->launches;
+  out->kernel = g->resident ? HSGA_KERNEL_RESIDENT : HSGA_KERNEL_STREAMED;
+  if (g->resident) {
+    out->islands_per_warp = (uint32_t)g->plan.ipw;
+    out->warps_per_block = (uint32_t)g->plan.warps_per_block;
+    out->blocks = (uint32_t)g->plan.blocks;
+  }
+  return HSGA_OK;
+}
+
+// Checkpoint layout: magic, config, G, then traits and surfaces.
+int hsga_save(hsga_grid *g, void *buf, size_t *len) {
+  if (!g || !len) return HSGA_ERR_INVALID_ARG;
+  const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 12;
+  if (!buf) {
+    *len = need;
+    return HSGA_OK;
+  }
+  if (*len < need) return HSGA_ERR_INVALID_ARG;
+  char *p = (char *)buf;
+  memcpy(p, &kCheckpointMagic, 8);
+  memcpy(p + 8, &g->cfg, sizeof(hsga_config));
+  memcpy(p + 8 + sizeof(hsga_config), &g->G, 8);
+  uint32_t *t = (uint32_t *)(p + 16 + sizeof(hsga_config));
+  uint64_t *s = (uint64_t *)(t + g->agents);
+  // surfaces may be unaligned for uint64 in the caller's buffer: stage via get_population
+  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (g->agents ? g->agents : 1));
+  if (!tmp) return HSGA_ERR_OOM;
+  int r = hsga_get_population(g, t, tmp);
+  if (r == HSGA_OK) memcpy(s, tmp, sizeof(uint64_t) * g->agents);
+  free(tmp);
+  if (r == HSGA_OK) *len = need;
+  return r;
+}
+
+int hsga_load(hsga_grid *g, const void *buf, size_t len) {
+  if (!g || !buf) return HSGA_ERR_INVALID_ARG;
+  const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 12;
+  if (len < need) return HSGA_ERR_INVALID_ARG;
+  const char *p = (const char *)buf;
+  uint64_t magic = 0, G = 0;
+  memcpy(&magic, p, 8);
+  if (magic != kCheckpointMagic) return HSGA_ERR_INVALID_ARG;
+  if (memcmp(p + 8, &g->cfg, sizeof(hsga_config)) != 0) return HSGA_ERR_INVALID_ARG;
+  memcpy(&G, p + 8 + sizeof(hsga_config), 8);
+  const uint32_t *t = (const uint32_t *)(p + 16 + sizeof(hsga_config));
+  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (g->agents ? g->agents : 1));
+  uint32_t *tt = (uint32_t *)malloc(sizeof(uint32_t) * (g->agents ? g->agents : 1));
+  if (!tmp || !tt) {
+    free(tmp);
+    free(tt);
+    return HSGA_ERR_OOM;
+  }
+  memcpy(tt, t, sizeof(uint32_t) * g->agents);
+  memcpy(tmp, t + g->agents, sizeof(uint64_t) * g->agents);
+  int r = hsga_set_population(g, tt, tmp, G);
+  free(tmp);
+  free(tt);
+  return r;
+}
+
+void hsga_destroy(hsga_grid *g) { free_grid(g); }
+
+uint32_t hsga_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T) {
+  if (policy > HSGA_NONE || !power_of_two(S) || S < 2) return S;
+  if ((policy == HSGA_TILTED || policy == HSGA_STRETCHED) && (!power_of_two(W) || S / W < 2))
+    return S;
+  return site_of(policy, S, W, T);
+}
+
+// Closed-form timestamp lookup (see hsga.h for the site functions it inverts).
+int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *out) {
+  if (!out || !power_of_two(S) || S < 2 || S > 64 || policy > HSGA_NONE)
+    return HSGA_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < S; ++i) out[i] = -1;
+  if (N == 0 || policy == HSGA_NONE) return HSGA_OK;
+  if (policy == HSGA_TRIVIAL) {
+    for (uint32_t p = 0; p < S; ++p)
+      if (N > p) out[p] = (int64_t)(p + S * ((N - 1 - p) / S));
+    return HSGA_OK;
+  }
+  if (policy == HSGA_STEADY) {
+    // After N depositions the current epoch is e = e(N-1).  Epoch-e items are
+    // times m 2^e - 1 (1 <= m <= S) at site (m 2^e mod S+1) - 1; those with
+    // m <= N / 2^e are in place, the other sites still hold the epoch-(e-1)
+    // item that maps there.  Inverting the site map needs 2^-e mod S+1, and
+    // 2^(2s) = 1 mod S+1 because 2^s = -1.
+    const uint32_t s = bitlen64(S) - 1;
+    const uint64_t M = (uint64_t)S + 1;
+    const uint32_t e = (N <= S) ? 0u : bitlen64(N - 1) - s;
+    if (e == 0) {
+      for (uint32_t p = 0; p < S && p < N; ++p) out[p] = p;
+      return HSGA_OK;
+    }
+    auto inv_pow2 = [&](uint32_t k) {  // 2^-k mod M
+      const uint32_t r = (2 * s - (k % (2 * s))) % (2 * s);
+      uint64_t v = 1;
+      for (uint32_t i = 0; i < r; ++i) v = (v * 2) % M;
+      return v;
+    };
+    const uint64_t ie = inv_pow2(e), ie1 = inv_pow2(e - 1);
+    const uint64_t cap = N >> e;
+    for (uint32_t p = 0; p < S; ++p) {
+      const uint64_t m = ((uint64_t)(p + 1) * ie) % M;
+      if (m >= 1 && m <= cap) {
+        out[p] = (int64_t)((m << e) - 1);
+      } else {
+        const uint64_t m1 = ((uint64_t)(p + 1) * ie1) % M;
+        out[p] = (int64_t)((m1 << (e - 1)) - 1);
+      }
+    }
+    return HSGA_OK;
+  }
+  // tilted / stretched
+  if (!power_of_two(W) || S / W < 2) return HSGA_ERR_INVALID_ARG;
+  const uint32_t L = S / W;
+  for (uint32_t lvl = 0; lvl < L; ++lvl) {
+    const bool capped = lvl == L - 1;
+    const uint64_t c = capped ? (N >> (L - 1)) : ((N + (1ull << lvl)) >> (lvl + 1));
+    for (uint32_t r = 0; r < W; ++r) {
+      uint64_t idx;
+      if (policy == HSGA_TILTED) {
+        if (c <= r) continue;
+        idx = r + (uint64_t)W * ((c - 1 - r) / W);
+      } else {
+        if (c <= r) continue;
+        idx = r;
+      }
+      out[lvl * W + r] = capped ? (int64_t)(((idx + 1) << (L - 1)) - 1)
+                                : (int64_t)(((2 * idx + 1) << lvl) - 1);
+    }
+  }
+  return HSGA_OK;
+}
+
+int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
+                      uint32_t *out_dev, void *cuda_stream) {
+  if (count > 0 && !out_dev) return HSGA_ERR_INVALID_ARG;
+  if (policy > HSGA_NONE || !power_of_two(S) || S < 2 || S > 64) return HSGA_ERR_INVALID_ARG;
+  if ((policy == HSGA_TILTED || policy == HSGA_STRETCHED) && (!power_of_two(W) || S / W < 2))
+    return HSGA_ERR_INVALID_ARG;
+  if (T0 + count >= 0xFFFFFFFFull) return HSGA_ERR_INVALID_ARG;
+  return cuda_status(launch_sites(policy, S, W, T0, count, out_dev, (cudaStream_t)cuda_stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// hsga_device.cuh -- device primitives of the island-model GA hot path
+// (arXiv 2404.10861): Philox4x32-10, uniform indices, surface site
+// functions, torus neighbours and the per-launch parameter block.
+#pragma once
+
+#include <stdint.h>
+
+#include "hsga.h"
+
+namespace hsga {
+
+// ---------------------------------------------------------------- RNG ---
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies whose high halves are xor'd into the other two words
+// with the round key; the key advances by the Weyl constants each round.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Counter purposes (word 3) and reserved slot values (word 0).
+constexpr uint32_t kPurposeMigration = 0;  // with kSlot* in word 0
+constexpr uint32_t kPurposeReplicate = 1;  // first tournament block
+constexpr uint32_t kPurposeSampleDraw = 3; // with island word 0xFFFFFFFF
+constexpr uint32_t kSlotEmigrant = 0xFFFFFFFFu;
+constexpr uint32_t kSlotImmigrant = 0xFFFFFFFEu;
+constexpr uint32_t kSlotSample = 0xFFFFFFFDu;
+
+struct Words4 {
+  uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ Words4 philox(uint32_t k0, uint32_t k1, uint32_t c0,
+                                                  uint32_t c1, uint32_t c2, uint32_t c3) {
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+  for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+#else
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0, p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
+// floor(w * m / 2^32): uniform index in [0, m) from one word.
+__host__ __device__ __forceinline__ uint32_t uindex(uint32_t w, uint32_t m) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(w, m);
+#else
+  return (uint32_t)(((uint64_t)w * m) >> 32);
+#endif
+}
+
+// ------------------------------------------------------------ surface ---
+__host__ __device__ __forceinline__ uint32_t bitlen64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return 64u - (uint32_t)__clzll((long long)x);
+#else
+  return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t ctz64(uint64_t x) {  // x > 0
+#ifdef __CUDA_ARCH__
+  return (uint32_t)__ffsll((long long)x) - 1u;
+#else
+  return (uint32_t)__builtin_ctzll(x);
+#endif
+}
+
+// Site of deposition T; S = discard.  See hsga.h for the readings.
+__host__ __device__ __forceinline__ uint32_t site_of(uint32_t policy, uint32_t S, uint32_t W,
+                                                     uint64_t T) {
+  const uint64_t t1 = T + 1;
+  switch (policy) {
+    case HSGA_TRIVIAL:
+      return (uint32_t)(T & (S - 1));
+    case HSGA_STEADY: {
+      const uint32_t s = bitlen64(S) - 1;
+      const uint32_t e = (t1 <= S) ? 0u : bitlen64(T) - s;
+      if (ctz64(t1) < e) return S;
+      return (uint32_t)(t1 % ((uint64_t)S + 1)) - 1u;
+    }
+    case HSGA_TILTED:
+    case HSGA_STRETCHED: {
+      const uint32_t L = S / W;
+      const uint32_t h = ctz64(t1);
+      uint32_t level;
+      uint64_t j;
+      if (h < L - 1) {
+        level = h;
+        j = t1 >> (h + 1);
+      } else {
+        level = L - 1;
+        j = (t1 >> (L - 1)) - 1;
+      }
+      if (policy == HSGA_TILTED) return level * W + (uint32_t)(j & (W - 1));
+      return j < W ? level * W + (uint32_t)j : S;
+    }
+    default:
+      return S;
+  }
+}
+
+// ------------------------------------------------------------- params ---
+// Everything a generation kernel needs that is fixed for a run.
+struct RunParams {
+  uint32_t rows, cols, n, islands;
+  uint32_t tournament;
+  uint32_t k0, k1;         // Philox key = seed
+  uint32_t policy, S, W, bits;
+  uint32_t interval;
+  uint64_t thr_ben;        // w2 <  thr_ben            -> trait + 1
+  uint64_t thr_bd;         // thr_ben <= w2 < thr_bd   -> trait - 1
+  uint64_t vmask;          // (1 << bits) - 1
+};
+
+// Per-generation deposit parameters: a whole synchronous generation shares T.
+struct Deposit {
+  uint64_t clear;  // bits kept from the parent surface
+  uint32_t shift;  // site * bits
+  uint32_t on;     // 0 when the policy discards this deposition
+};
+
+__host__ __device__ __forceinline__ Deposit deposit_for(const RunParams &p, uint64_t T) {
+  Deposit d{~0ull, 0u, 0u};
+  if (p.policy == HSGA_NONE) return d;
+  const uint32_t site = site_of(p.policy, p.S, p.W, T);
+  if (site >= p.S) return d;
+  d.shift = site * p.bits;
+  d.clear = ~(p.vmask << d.shift);
+  d.on = 1u;
+  return d;
+}
+
+// Neighbour of island `isl` in direction d (0 N, 1 E, 2 S, 3 W).
+__host__ __device__ __forceinline__ uint32_t neighbour(const RunParams &p, uint32_t isl,
+                                                       uint32_t d) {
+  uint32_t r = isl / p.cols, c = isl - r * p.cols;
+  if (d == 0) r = (r == 0) ? p.rows - 1 : r - 1;
+  else if (d == 2) r = (r + 1 == p.rows) ? 0 : r + 1;
+  else if (d == 1) c = (c + 1 == p.cols) ? 0 : c + 1;
+  else c = (c == 0) ? p.cols - 1 : c - 1;
+  return r * p.cols + c;
+}
+
+__host__ __device__ __forceinline__ bool migrates(const RunParams &p, uint64_t G) {
+  return p.interval != 0 && (G % p.interval) == 0;
+}
+
+// a5: saturating +1 / -1 from the mutation word.
+__device__ __forceinline__ uint32_t mutate(const RunParams &p, uint32_t trait, uint32_t w2) {
+  if ((uint64_t)w2 < p.thr_ben) return trait + (trait != 0xFFFFFFFFu ? 1u : 0u);
+  if ((uint64_t)w2 < p.thr_bd) return trait - (trait != 0u ? 1u : 0u);
+  return trait;
+}
+
+// Device error word values (first error wins).
+constexpr int kDevErrWaitTimeout = 1;
+constexpr int kDevErrState = 2;
+
+}  // namespace hsga

@@ -1,0 +1,49 @@
+// hsga_internal.h -- kernel launch interface between the C-ABI runtime
+// (hsga_capi.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "hsga_device.cuh"
+
+namespace hsga {
+
+constexpr int kStreamThreads = 256;     // streamed kernel block: 8 warps = 8 islands in flight
+constexpr int kResidentThreads = 128;   // resident kernel block: 4 warps
+constexpr uint32_t kSampleSmemMax = 12288;  // largest k sampled by the shared-memory kernel
+constexpr uint64_t kWaitNs = 1000000000ull; // bounded device wait: 1 s
+
+struct ResidentPlan {
+  int ap = 0;      // agents per lane (1: n <= 32, 2: n <= 64)
+  int ipw = 0;     // islands per warp
+  int blocks = 0;  // cooperative grid
+  int warps_per_block = kResidentThreads / 32;
+};
+
+cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
+                                 const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
+                                 uint64_t *sout, cudaStream_t stream);
+
+// Chooses the resident tile (smallest islands-per-warp whose cooperative
+// grid is co-resident).  Returns false when the grid does not fit on chip.
+bool resident_plan(const RunParams &p, ResidentPlan *out);
+
+cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
+                                 uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
+                                 uint4 *rec, uint32_t *flags, int *err, cudaStream_t stream);
+
+cudaError_t launch_migrate(const RunParams &p, uint32_t G, uint32_t *t, uint64_t *s,
+                           uint4 *rec, cudaStream_t stream);
+
+size_t sample_scratch_bytes(const RunParams &p, uint32_t k);
+
+cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint32_t *t,
+                          const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
+                          uint32_t *scratch, cudaStream_t stream);
+
+cudaError_t launch_sites(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
+                         uint32_t *out, cudaStream_t stream);
+
+}  // namespace hsga

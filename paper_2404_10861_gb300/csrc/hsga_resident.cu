@@ -1,0 +1,254 @@
+// hsga_resident.cu -- persistent resident generation kernel.
+//
+// One cooperative launch advances many synchronous generations.  Each warp
+// owns IPW islands and keeps their genomes in registers for the whole launch
+// (lane l: agents l and l+32).  There is no grid-wide barrier: islands only
+// depend on their four neighbours' emigrants, so each island publishes its
+// emigrant as a 16-byte record (one 128-bit store) into a slot double-
+// buffered by migration parity, then raises its sequence flag with a release
+// store; a receiver acquires the four neighbour flags before reading their
+// records.  An island can run at most one migration ahead of a neighbour,
+// which is why two record buffers suffice: a record of migration m is only
+// overwritten at m+2, after the writer has read the reader's m+1 record,
+// which the reader publishes only after it has consumed the m record.
+//
+// Every wait is bounded (1 s of %globaltimer); on expiry the warp records a
+// timeout in the grid's error word and leaves, which lets its neighbours
+// time out in turn.  The cooperative launch guarantees that every island's
+// warp is resident, so waits only expire on an inconsistent state.
+#include <cuda_runtime.h>
+
+#include "hsga_internal.h"
+#include "hsga_island.cuh"
+
+namespace hsga {
+
+constexpr uint32_t kChunk = 16;  // generations whose per-island RNG blocks are batched
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *flag >= seq.  Returns false on timeout or when
+// another warp already reported an error.
+__device__ bool wait_flag(const uint32_t *flag, uint32_t seq, const int *err) {
+  if (ld_acquire(flag) >= seq) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (ld_acquire(flag) >= seq) return true;
+    if (*(volatile const int *)err != 0) return false;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+template <int AP, int IPW, bool TRACKED>
+__global__ void __launch_bounds__(kResidentThreads)
+    step_resident_kernel(RunParams p, uint32_t G0, uint32_t ngen, int premigrated,
+                         uint32_t *__restrict__ tplane, uint64_t *__restrict__ splane,
+                         uint4 *__restrict__ rec, uint32_t *__restrict__ flags,
+                         int *__restrict__ err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = blockIdx.x * (kResidentThreads / 32) + (threadIdx.x >> 5);
+  uint32_t isl[IPW];
+  uint32_t pt[IPW][AP];
+  uint64_t ps[IPW][AP];
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    isl[k] = warp * IPW + k;
+#pragma unroll
+    for (int a = 0; a < AP; ++a) {
+      const uint32_t j = lane + 32u * a;
+      pt[k][a] = 0;
+      ps[k][a] = 0;
+      if (isl[k] < p.islands && j < p.n) {
+        pt[k][a] = tplane[(size_t)isl[k] * p.n + j];
+        if constexpr (TRACKED) ps[k][a] = splane[(size_t)isl[k] * p.n + j];
+      }
+    }
+  }
+  const bool any_mig = p.interval != 0;
+  bool failed = false;
+
+  for (uint32_t g0 = 0; g0 < ngen && !failed; g0 += kChunk) {
+    // Batched per-chunk draws: lane o (< 16) holds the emigrant block of
+    // generation G0+g0+o, lane 16+o its placement block; every lane holds
+    // the deposit of generation G0+g0+(lane & 15), packed as site*b | on<<8.
+    const uint32_t Gl = G0 + g0 + (lane & (kChunk - 1));
+    const Deposit dl = deposit_for(p, Gl);
+    const uint32_t dpack = dl.on ? (dl.shift | 0x100u) : 0u;
+    Words4 mig[IPW];
+#pragma unroll
+    for (int k = 0; k < IPW; ++k) {
+      mig[k] = Words4{0, 0, 0, 0};
+      if (any_mig && isl[k] < p.islands)
+        mig[k] = philox(p.k0, p.k1, lane < kChunk ? kSlotEmigrant : kSlotImmigrant, isl[k], Gl,
+                        kPurposeMigration);
+    }
+    const uint32_t steps = min(kChunk, ngen - g0);
+    for (uint32_t o = 0; o < steps; ++o) {
+      const uint32_t G = G0 + g0 + o;
+      const uint32_t dp = __shfl_sync(kFull, dpack, o);
+      Deposit dep;
+      dep.on = dp >> 8;
+      dep.shift = dp & 0xFFu;
+      dep.clear = ~(p.vmask << dep.shift);
+      const bool do_mig = migrates(p, G) && !(premigrated && g0 + o == 0);
+      uint32_t buf = 0, seq = 0;
+      if (do_mig) {
+        const uint32_t m_idx = G / p.interval;
+        buf = m_idx & 1u;
+        seq = m_idx + 1u;
+        // a1: publish every owned island's emigrant before reading any.
+#pragma unroll
+        for (int k = 0; k < IPW; ++k) {
+          if (isl[k] >= p.islands) continue;
+          const uint32_t eslot = uindex(__shfl_sync(kFull, mig[k].x, o), p.n);
+          const uint32_t dir = __shfl_sync(kFull, mig[k].y, o) >> 30;
+          if (lane == (eslot & 31u)) {
+            uint32_t tv = pt[k][0];
+            uint64_t sv = ps[k][0];
+            if constexpr (AP == 2) {
+              if (eslot >> 5) {
+                tv = pt[k][1];
+                sv = ps[k][1];
+              }
+            }
+            rec[(size_t)buf * p.islands + isl[k]] =
+                make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
+            st_release(flags + isl[k], seq);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < IPW; ++k) {
+        if (isl[k] >= p.islands) continue;
+        Words4 w[AP];
+        replication_words<AP>(p, isl[k], G, w);
+        if (do_mig) {
+          // a2: lanes 0..3 take the neighbour records in directions N, E, S, W.
+          bool ok = true, arrive = false;
+          uint32_t it = 0;
+          uint64_t is = 0;
+          if (lane < 4) {
+            const uint32_t nb = neighbour(p, isl[k], lane);
+            ok = wait_flag(flags + nb, seq, err);
+            if (ok) {
+              const uint4 r = __ldcg(rec + (size_t)buf * p.islands + nb);
+              arrive = r.w == ((lane + 2u) & 3u);
+              it = r.x;
+              is = ((uint64_t)r.z << 32) | r.y;
+            }
+          }
+          if (__any_sync(kFull, !ok)) {
+            if (lane == 0) atomicCAS(err, 0, kDevErrWaitTimeout);
+            failed = true;
+            break;
+          }
+          const uint32_t arrivals = __ballot_sync(kFull, arrive);
+          const uint32_t place[4] = {mig[k].x, mig[k].y, mig[k].z, mig[k].w};
+#pragma unroll
+          for (uint32_t dd = 0; dd < 4; ++dd) {
+            if (arrivals & (1u << dd)) {
+              const uint32_t slot = uindex(__shfl_sync(kFull, place[dd], kChunk + o), p.n);
+              land<AP, TRACKED>(slot, dd, it, is, pt[k], ps[k]);
+            }
+          }
+        }
+        uint32_t ct[AP];
+        uint64_t cs[AP];
+        replicate<AP, TRACKED>(p, dep, isl[k], G, w, pt[k], ps[k], ct, cs);
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          pt[k][a] = ct[a];
+          ps[k][a] = cs[a];
+        }
+      }
+      if (failed) break;
+    }
+  }
+  if (failed) return;
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+#pragma unroll
+    for (int a = 0; a < AP; ++a) {
+      const uint32_t j = lane + 32u * a;
+      if (isl[k] < p.islands && j < p.n) {
+        tplane[(size_t)isl[k] * p.n + j] = pt[k][a];
+        if constexpr (TRACKED) splane[(size_t)isl[k] * p.n + j] = ps[k][a];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- launch ---
+using ResidentFn = void (*)(RunParams, uint32_t, uint32_t, int, uint32_t *, uint64_t *, uint4 *,
+                            uint32_t *, int *);
+
+static ResidentFn pick(int ap, int ipw, bool tracked) {
+#define HSGA_PICK(AP_, IPW_)                                                       \
+  if (ap == AP_ && ipw == IPW_)                                                    \
+    return tracked ? step_resident_kernel<AP_, IPW_, true> : step_resident_kernel<AP_, IPW_, false>;
+  HSGA_PICK(1, 1)
+  HSGA_PICK(1, 2)
+  HSGA_PICK(1, 4)
+  HSGA_PICK(2, 1)
+  HSGA_PICK(2, 2)
+#undef HSGA_PICK
+  return nullptr;
+}
+
+bool resident_plan(const RunParams &p, ResidentPlan *out) {
+  int dev = 0, sms = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return false;
+  const int ap = p.n <= 32 ? 1 : 2;
+  const int wpb = kResidentThreads / 32;
+  const int ipws[3] = {1, 2, 4};
+  for (int ipw : ipws) {
+    ResidentFn fn = pick(ap, ipw, p.policy != HSGA_NONE);
+    if (!fn) continue;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResidentThreads, 0) !=
+        cudaSuccess)
+      return false;
+    const uint64_t warps = ((uint64_t)p.islands + ipw - 1) / ipw;
+    const uint64_t blocks = (warps + wpb - 1) / wpb;
+    if (per_sm > 0 && blocks <= (uint64_t)per_sm * sms) {
+      out->ap = ap;
+      out->ipw = ipw;
+      out->blocks = (int)blocks;
+      out->warps_per_block = wpb;
+      return true;
+    }
+  }
+  return false;
+}
+
+cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
+                                 uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
+                                 uint4 *rec, uint32_t *flags, int *err, cudaStream_t stream) {
+  ResidentFn fn = pick(plan.ap, plan.ipw, p.policy != HSGA_NONE);
+  if (!fn) return cudaErrorInvalidValue;
+  RunParams pp = p;
+  int prem = premigrated ? 1 : 0;
+  void *args[] = {&pp, &G0, &ngen, &prem, &t, &s, &rec, &flags, &err};
+  return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.blocks),
+                                     dim3(kResidentThreads), args, 0, stream);
+}
+
+}  // namespace hsga
