@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ROWS, COLS, N_AGENTS = 512, 1024, 32
-GENS_PER_STEP = 100
+GENS_PER_STEP = 200
 SAMPLE_K = 10000
 WORKLOAD = dict(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy="tilted", bits=1, W=2,
                 interval=1, p_ben=1e-3, p_del=0.0)
@@ -326,7 +326,7 @@ def run_profile(gens: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -35,6 +35,8 @@
  *     CUDA runtime which one it is and copies accordingly.  The caller owns
  *     every buffer it passes; the library owns the grid and its buffers
  *     until hsga_destroy().
+ *   - rows * cols * agents_per_island must stay below 2^32 - 1 (agent
+ *     offsets are 32-bit on the device).
  *   - Genome record (the paper's 128-bit layout, section "Genome Model"):
  *     4 x uint32 = [trait, surface bits 0..31, surface bits 32..63, T].
  *     Differentia of site p occupies surface bits [p*b, p*b + b).

@@ -87,6 +87,9 @@ int validate(const hsga_config *c) {
   if (c->rows == 0 || c->cols == 0) return HSGA_ERR_INVALID_ARG;
   if ((uint64_t)c->rows * c->cols >= 0xFFFFFFF0ull) return HSGA_ERR_INVALID_ARG;
   if (c->agents_per_island == 0 || c->agents_per_island > 64) return HSGA_ERR_INVALID_ARG;
+  // agent offsets are 32-bit in the kernels
+  if ((uint64_t)c->rows * c->cols * c->agents_per_island >= 0xFFFFFFFFull)
+    return HSGA_ERR_INVALID_ARG;
   if (c->tournament_size == 0 || c->tournament_size > 64) return HSGA_ERR_INVALID_ARG;
   if (c->surface_policy > HSGA_NONE) return HSGA_ERR_INVALID_ARG;
   const uint32_t b = c->differentia_bits;
@@ -120,9 +123,15 @@ RunParams make_params(const hsga_config *c) {
             ? c->sites_per_level
             : 2;
   p.interval = c->migration_interval;
-  p.thr_ben = threshold(c->p_beneficial);
-  p.thr_bd = p.thr_ben + threshold(c->p_deleterious);
+  const uint64_t thr_ben = threshold(c->p_beneficial);
+  const uint64_t thr_bd = thr_ben + threshold(c->p_deleterious);  // <= 2^32 (validated)
+  p.ben32 = (uint32_t)thr_ben;
+  p.ben_all = thr_ben >= (1ull << 32) ? 1u : 0u;
+  p.bd32 = (uint32_t)thr_bd;
+  p.bd_all = thr_bd >= (1ull << 32) ? 1u : 0u;
   p.vmask = (1ull << p.bits) - 1;
+  p.cols_div = make_fastdiv(p.cols);
+  set_round_keys(p);
   return p;
 }
 

@@ -117,6 +117,35 @@ __host__ __device__ __forceinline__ uint32_t site_of(uint32_t policy, uint32_t S
 }
 
 // ------------------------------------------------------------- params ---
+// Unsigned division by a run-invariant divisor with one multiply-high
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, section 4): for 1 <= d < 2^32 with
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, the quotient of any
+// 32-bit n is (t + ((n - t) >> min(l,1))) >> max(l-1,0), t = mulhi(m, n).
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fastdiv(const FastDiv &f, uint32_t n) {
+#ifdef __CUDA_ARCH__
+  const uint32_t t = __umulhi(f.m, n);
+#else
+  const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // Everything a generation kernel needs that is fixed for a run.
 struct RunParams {
   uint32_t rows, cols, n, islands;
@@ -124,33 +153,80 @@ struct RunParams {
   uint32_t k0, k1;         // Philox key = seed
   uint32_t policy, S, W, bits;
   uint32_t interval;
-  uint64_t thr_ben;        // w2 <  thr_ben            -> trait + 1
-  uint64_t thr_bd;         // thr_ben <= w2 < thr_bd   -> trait - 1
+  // a5 thresholds floor(p 2^32) in [0, 2^32]: w2 < thr is (w2 < thr32) || thr_all
+  uint32_t ben32, ben_all;  // beneficial: w2 < floor(p_ben 2^32)
+  uint32_t bd32, bd_all;    // deleterious: otherwise w2 < floor(p_ben 2^32) + floor(p_del 2^32)
   uint64_t vmask;          // (1 << bits) - 1
+  FastDiv cols_div;        // island -> (row, column)
+  uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (W0, W1)
 };
 
-// Per-generation deposit parameters: a whole synchronous generation shares T.
+inline void set_round_keys(RunParams &p) {
+  uint32_t a = p.k0, b = p.k1;
+  for (int r = 0; r < 10; ++r) {
+    p.rk0[r] = a;
+    p.rk1[r] = b;
+    a += kPhiloxW0;
+    b += kPhiloxW1;
+  }
+}
+
+// Philox4x32-10 with the run's precomputed round keys (same values as
+// philox(p.k0, p.k1, ...)); the keys stay in the kernel's parameter space.
+__device__ __forceinline__ Words4 philox_rk(const RunParams &p, uint32_t c0, uint32_t c1,
+                                            uint32_t c2, uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)c0 * kPhiloxM0;  // one 32x32->64 multiply each
+    const uint64_t p1 = (uint64_t)c2 * kPhiloxM1;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ p.rk0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ p.rk1[r];
+    c0 = n0;
+    c1 = (uint32_t)p1;
+    c2 = n2;
+    c3 = (uint32_t)p0;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
+// Per-generation deposit parameters: a whole synchronous generation shares
+// T, hence the site.  The b-bit field never straddles the two 32-bit halves
+// of the surface (b divides 32), so the insert is one bit-select per half:
+// half = (half & clear) | ((w3 << shift) & ~clear), with clear = all ones for
+// the half not written (or for a discarded deposition).
 struct Deposit {
-  uint64_t clear;  // bits kept from the parent surface
-  uint32_t shift;  // site * bits
-  uint32_t on;     // 0 when the policy discards this deposition
+  uint32_t clear_lo, clear_hi;  // bits of each half kept from the parent
+  uint32_t shift;               // (site * b) mod 32
 };
+
+__host__ __device__ __forceinline__ Deposit deposit_from_bit(uint32_t on, uint32_t bit,
+                                                             uint32_t vmask) {
+  Deposit d;
+  d.shift = bit & 31u;
+  const uint32_t field = on ? (vmask << d.shift) : 0u;
+  d.clear_lo = (bit >> 5) ? 0xFFFFFFFFu : ~field;
+  d.clear_hi = (bit >> 5) ? ~field : 0xFFFFFFFFu;
+  return d;
+}
 
 __host__ __device__ __forceinline__ Deposit deposit_for(const RunParams &p, uint64_t T) {
-  Deposit d{~0ull, 0u, 0u};
-  if (p.policy == HSGA_NONE) return d;
+  if (p.policy == HSGA_NONE) return deposit_from_bit(0u, 0u, (uint32_t)p.vmask);
   const uint32_t site = site_of(p.policy, p.S, p.W, T);
-  if (site >= p.S) return d;
-  d.shift = site * p.bits;
-  d.clear = ~(p.vmask << d.shift);
-  d.on = 1u;
-  return d;
+  if (site >= p.S) return deposit_from_bit(0u, 0u, (uint32_t)p.vmask);
+  return deposit_from_bit(1u, site * p.bits, (uint32_t)p.vmask);
+}
+
+__device__ __forceinline__ uint64_t deposit_into(const Deposit &d, uint64_t s, uint32_t w3) {
+  const uint32_t v = w3 << d.shift;
+  const uint32_t lo = ((uint32_t)s & d.clear_lo) | (v & ~d.clear_lo);
+  const uint32_t hi = ((uint32_t)(s >> 32) & d.clear_hi) | (v & ~d.clear_hi);
+  return ((uint64_t)hi << 32) | lo;
 }
 
 // Neighbour of island `isl` in direction d (0 N, 1 E, 2 S, 3 W).
 __host__ __device__ __forceinline__ uint32_t neighbour(const RunParams &p, uint32_t isl,
                                                        uint32_t d) {
-  uint32_t r = isl / p.cols, c = isl - r * p.cols;
+  uint32_t r = fastdiv(p.cols_div, isl), c = isl - r * p.cols;
   if (d == 0) r = (r == 0) ? p.rows - 1 : r - 1;
   else if (d == 2) r = (r + 1 == p.rows) ? 0 : r + 1;
   else if (d == 1) c = (c + 1 == p.cols) ? 0 : c + 1;
@@ -162,11 +238,14 @@ __host__ __device__ __forceinline__ bool migrates(const RunParams &p, uint64_t G
   return p.interval != 0 && (G % p.interval) == 0;
 }
 
-// a5: saturating +1 / -1 from the mutation word.
+// a5: saturating +1 / -1 from the mutation word (thresholds are ordered,
+// floor(p_ben 2^32) <= floor(p_ben 2^32) + floor(p_del 2^32)).
 __device__ __forceinline__ uint32_t mutate(const RunParams &p, uint32_t trait, uint32_t w2) {
-  if ((uint64_t)w2 < p.thr_ben) return trait + (trait != 0xFFFFFFFFu ? 1u : 0u);
-  if ((uint64_t)w2 < p.thr_bd) return trait - (trait != 0u ? 1u : 0u);
-  return trait;
+  const uint32_t ben = (uint32_t)(w2 < p.ben32) | p.ben_all;
+  const uint32_t bd = (uint32_t)(w2 < p.bd32) | p.bd_all;
+  const uint32_t inc = ben & (uint32_t)(trait != 0xFFFFFFFFu);
+  const uint32_t dec = bd & (ben ^ 1u) & (uint32_t)(trait != 0u);
+  return trait + inc - dec;
 }
 
 // Device error word values (first error wins).

@@ -45,14 +45,14 @@ __device__ __forceinline__ void replication_words(const RunParams &p, uint32_t i
   const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll
   for (int a = 0; a < AP; ++a)
-    w[a] = philox(p.k0, p.k1, lane + 32u * a, isl, G, kPurposeReplicate);
+    w[a] = philox_rk(p, lane + 32u * a, isl, G, kPurposeReplicate);
 }
 
 // a3-a6 for one island: parents (pt, ps) -> children (ct, cs).  Every lane
 // runs the same shuffles; children of lanes at or beyond n are garbage and
 // are never stored.  Candidate indices are always < n, so only loaded
-// parents are ever read.
-template <int AP, bool TRACKED>
+// parents are ever read.  T2: the tournament size is exactly 2.
+template <int AP, bool TRACKED, bool T2 = false>
 __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep, uint32_t isl,
                                           uint32_t G, const Words4 (&w)[AP],
                                           const uint32_t (&pt)[AP], const uint64_t (&ps)[AP],
@@ -64,26 +64,27 @@ __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep
     // drawn candidate keeps ties.
     uint32_t best = uindex(w[a].x, n);
     uint32_t fbest = fetch32<AP>(pt, best);
-    if (p.tournament >= 2) {
+    if (T2 || p.tournament >= 2) {
       const uint32_t c = uindex(w[a].y, n);
       const uint32_t fc = fetch32<AP>(pt, c);
-      if (fc > fbest) {
-        best = c;
-        fbest = fc;
-      }
+      const bool take = fc > fbest;
+      best = take ? c : best;
+      fbest = take ? fc : fbest;
     }
-    for (uint32_t c0 = 2; c0 < p.tournament; c0 += 4) {
-      const uint32_t j = (threadIdx.x & 31u) + 32u * a;
-      const Words4 e = philox(p.k0, p.k1, j, isl, G, kPurposeReplicate + 1 + (c0 - 2) / 4);
-      const uint32_t ew[4] = {e.x, e.y, e.z, e.w};
+    if constexpr (!T2) {
+      for (uint32_t c0 = 2; c0 < p.tournament; c0 += 4) {
+        const uint32_t j = (threadIdx.x & 31u) + 32u * a;
+        const Words4 e = philox_rk(p, j, isl, G, kPurposeReplicate + 1 + (c0 - 2) / 4);
+        const uint32_t ew[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (c0 + r < p.tournament) {
-          const uint32_t c = uindex(ew[r], n);
-          const uint32_t fc = fetch32<AP>(pt, c);
-          if (fc > fbest) {
-            best = c;
-            fbest = fc;
+        for (int r = 0; r < 4; ++r) {
+          if (c0 + r < p.tournament) {
+            const uint32_t c = uindex(ew[r], n);
+            const uint32_t fc = fetch32<AP>(pt, c);
+            if (fc > fbest) {
+              best = c;
+              fbest = fc;
+            }
           }
         }
       }
@@ -91,13 +92,8 @@ __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep
     // a5: mutation of the winner's trait.
     ct[a] = mutate(p, fbest, w[a].z);
     // a6: the child inherits the winner's surface plus one new differentia.
-    if constexpr (TRACKED) {
-      uint64_t s = fetch64<AP>(ps, best);
-      if (dep.on) s = (s & dep.clear) | ((uint64_t)(w[a].w & (uint32_t)p.vmask) << dep.shift);
-      cs[a] = s;
-    } else {
-      cs[a] = 0;
-    }
+    if constexpr (TRACKED) cs[a] = deposit_into(dep, fetch64<AP>(ps, best), w[a].w);
+    else cs[a] = 0;
   }
 }
 

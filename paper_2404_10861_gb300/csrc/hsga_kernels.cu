@@ -16,91 +16,216 @@
 namespace hsga {
 
 // ------------------------------------------------------ streamed step ---
-// a1+a2 of island `isl` read from the parent planes: lanes 0..3 evaluate
-// the emigrant block of the neighbour in direction `lane` and gather its
-// genome when it is aimed at `isl`; lane 4 evaluates the island's placement
-// block; arrivals land in direction order N, E, S, W.
-template <int AP, bool TRACKED>
-__device__ __forceinline__ void immigrate_from_planes(const RunParams &p, uint32_t isl, uint32_t G,
-                                                      const uint32_t *__restrict__ tin,
-                                                      const uint64_t *__restrict__ sin,
-                                                      uint32_t (&pt)[AP], uint64_t (&ps)[AP]) {
+// A warp advances groups of kGroup consecutive islands.  The group's
+// migration draws take one warp-wide Philox evaluation: lane 5p+r (r < 4)
+// evaluates the emigrant block of the neighbour in direction r of island
+// isl0+p and gathers that emigrant's genome from the parent planes when it is
+// aimed at isl0+p; lane 5p+4 evaluates the placement block of isl0+p and
+// turns it into a landing plan: byte d holds the slot where the direction-d
+// immigrant ends up, or 0xFF when it does not arrive or a later direction
+// lands on the same slot (later arrivals overwrite earlier ones).
+constexpr uint32_t kGroup = 6;  // 6 islands x 5 blocks = 30 of 32 lanes
+
+struct GroupMigration {
+  uint32_t plan;  // lane 5p+4: landing plan of island isl0+p
+  uint32_t it;    // lane 5p+r: the direction-r immigrant's genome
+  uint64_t is;
+};
+
+template <bool TRACKED>
+__device__ __forceinline__ void group_migration(const RunParams &p, uint32_t isl0, uint32_t G,
+                                                const uint32_t *__restrict__ tin,
+                                                const uint64_t *__restrict__ sin,
+                                                GroupMigration &gm) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t d = lane & 3u;
-  const uint32_t nb = neighbour(p, isl, d);
-  const Words4 m = philox(p.k0, p.k1, lane == 4 ? kSlotImmigrant : kSlotEmigrant,
-                          lane == 4 ? isl : nb, G, kPurposeMigration);
-  const bool arrive = lane < 4 && (m.y >> 30) == ((d + 2u) & 3u);
-  uint32_t it = 0;
-  uint64_t is = 0;
+  const uint32_t pi = lane / 5u, role = lane - pi * 5u;
+  const uint32_t isl = isl0 + pi;
+  const bool valid = lane < 5u * kGroup && isl < p.islands;
+  const uint32_t src = valid ? (role == 4 ? isl : neighbour(p, isl, role)) : 0u;
+  const Words4 m =
+      philox_rk(p, role == 4 ? kSlotImmigrant : kSlotEmigrant, src, G, kPurposeMigration);
+  const bool arrive = valid && role < 4 && (m.y >> 30) == ((role + 2u) & 3u);
+  gm.it = 0;
+  gm.is = 0;
   if (arrive) {
-    const size_t src = (size_t)nb * p.n + uindex(m.x, p.n);
-    it = __ldg(tin + src);
-    if constexpr (TRACKED) is = __ldg(sin + src);
+    const uint32_t a = src * p.n + uindex(m.x, p.n);
+    gm.it = __ldg(tin + a);
+    if constexpr (TRACKED) gm.is = __ldg(sin + a);
   }
   const uint32_t arrivals = __ballot_sync(kFull, arrive);
-  if (arrivals == 0) return;
-  const uint32_t placement[4] = {m.x, m.y, m.z, m.w};
+  const uint32_t bits = (arrivals >> (5u * pi)) & 0xFu;
+  uint32_t b[4] = {uindex(m.x, p.n), uindex(m.y, p.n), uindex(m.z, p.n), uindex(m.w, p.n)};
 #pragma unroll
-  for (uint32_t dd = 0; dd < 4; ++dd) {
-    if (arrivals & (1u << dd)) {
-      const uint32_t slot = uindex(__shfl_sync(kFull, placement[dd], 4), p.n);
-      land<AP, TRACKED>(slot, dd, it, is, pt, ps);
+  for (int d = 0; d < 4; ++d)
+    if (!((bits >> d) & 1u)) b[d] = 0xFFu;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int e = d + 1; e < 4; ++e)
+      if (b[e] == b[d]) b[d] = 0xFFu;
+  gm.plan = (role == 4 && valid) ? (b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24))
+                                 : 0xFFFFFFFFu;
+}
+
+// a2 for island isl0+k: each lane looks its slots up in the landing plan
+// (a zero-byte test on plan ^ slot) and pulls the immigrant from the lane that
+// gathered it.
+template <int AP, bool TRACKED>
+__device__ __forceinline__ void group_land(const GroupMigration &gm, uint32_t k,
+                                           uint32_t (&pt)[AP], uint64_t (&ps)[AP]) {
+  const uint32_t plan = __shfl_sync(kFull, gm.plan, 5u * k + 4u);
+  if (plan == 0xFFFFFFFFu) return;
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int a = 0; a < AP; ++a) {
+    const uint32_t x = plan ^ ((lane + 32u * a) * 0x01010101u);
+    // lowest zero byte of x (at most one byte can match: plan bytes of
+    // surviving directions are distinct)
+    const uint32_t z = (x - 0x01010101u) & ~x & 0x80808080u;
+    const uint32_t d = (uint32_t)(__ffs(z) - 1) >> 3;
+    const uint32_t src = z ? 5u * k + d : lane;
+    const uint32_t vt = __shfl_sync(kFull, gm.it, src);
+    if (z) pt[a] = vt;
+    if constexpr (TRACKED) {
+      const uint64_t vs = shfl64(gm.is, src);
+      if (z) ps[a] = vs;
     }
   }
 }
 
 template <int AP, bool TRACKED>
+__device__ __forceinline__ void load_island(const RunParams &p, uint32_t isl,
+                                            const uint32_t *__restrict__ tin,
+                                            const uint64_t *__restrict__ sin, uint32_t (&t)[AP],
+                                            uint64_t (&s)[AP]) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t base = isl * p.n;
+#pragma unroll
+  for (int a = 0; a < AP; ++a) {
+    const uint32_t j = lane + 32u * a;
+    t[a] = 0;
+    s[a] = 0;
+    if (j < p.n) {
+      t[a] = __ldcs(tin + base + j);
+      if constexpr (TRACKED) s[a] = __ldcs(sin + base + j);
+    }
+  }
+}
+
+template <int AP, bool TRACKED>
+__device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
+                                             uint32_t *__restrict__ tout,
+                                             uint64_t *__restrict__ sout,
+                                             const uint32_t (&t)[AP], const uint64_t (&s)[AP]) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t base = isl * p.n;
+#pragma unroll
+  for (int a = 0; a < AP; ++a) {
+    const uint32_t j = lane + 32u * a;
+    if (j < p.n) {
+      __stcs(tout + base + j, t[a]);
+      if constexpr (TRACKED) __stcs(sout + base + j, s[a]);
+    }
+  }
+}
+
+// One full group: all six islands' genomes are requested up front (deep
+// memory-level parallelism), then the islands are processed in pairs so that
+// each lane runs two independent Philox chains.
+template <int AP, bool TRACKED, bool T2>
+__device__ __forceinline__ void full_group(const RunParams &p, const Deposit &dep, uint32_t G,
+                                           bool do_mig, uint32_t isl0,
+                                           const uint32_t *__restrict__ tin,
+                                           const uint64_t *__restrict__ sin,
+                                           uint32_t *__restrict__ tout,
+                                           uint64_t *__restrict__ sout) {
+  uint32_t pt[kGroup][AP];
+  uint64_t ps[kGroup][AP];
+#pragma unroll
+  for (uint32_t k = 0; k < kGroup; ++k) load_island<AP, TRACKED>(p, isl0 + k, tin, sin, pt[k], ps[k]);
+  GroupMigration gm;
+  if (do_mig) group_migration<TRACKED>(p, isl0, G, tin, sin, gm);
+#pragma unroll
+  for (uint32_t k = 0; k < kGroup; k += 2) {
+    Words4 wa[AP], wb[AP];
+    replication_words<AP>(p, isl0 + k, G, wa);
+    replication_words<AP>(p, isl0 + k + 1, G, wb);
+    if (do_mig) {
+      group_land<AP, TRACKED>(gm, k, pt[k], ps[k]);
+      group_land<AP, TRACKED>(gm, k + 1, pt[k + 1], ps[k + 1]);
+    }
+    uint32_t ct[2][AP];
+    uint64_t cs[2][AP];
+    replicate<AP, TRACKED, T2>(p, dep, isl0 + k, G, wa, pt[k], ps[k], ct[0], cs[0]);
+    replicate<AP, TRACKED, T2>(p, dep, isl0 + k + 1, G, wb, pt[k + 1], ps[k + 1], ct[1], cs[1]);
+    store_island<AP, TRACKED>(p, isl0 + k, tout, sout, ct[0], cs[0]);
+    store_island<AP, TRACKED>(p, isl0 + k + 1, tout, sout, ct[1], cs[1]);
+  }
+}
+
+// The last, partial group: islands one at a time.
+template <int AP, bool TRACKED, bool T2>
+__device__ __noinline__ void partial_group(const RunParams &p, const Deposit &dep, uint32_t G,
+                                           bool do_mig, uint32_t isl0,
+                                           const uint32_t *__restrict__ tin,
+                                           const uint64_t *__restrict__ sin,
+                                           uint32_t *__restrict__ tout,
+                                           uint64_t *__restrict__ sout) {
+  GroupMigration gm;
+  if (do_mig) group_migration<TRACKED>(p, isl0, G, tin, sin, gm);
+  for (uint32_t k = 0; isl0 + k < p.islands; ++k) {
+    uint32_t pt[AP], ct[AP];
+    uint64_t ps[AP], cs[AP];
+    load_island<AP, TRACKED>(p, isl0 + k, tin, sin, pt, ps);
+    Words4 w[AP];
+    replication_words<AP>(p, isl0 + k, G, w);
+    if (do_mig) group_land<AP, TRACKED>(gm, k, pt, ps);
+    replicate<AP, TRACKED, T2>(p, dep, isl0 + k, G, w, pt, ps, ct, cs);
+    store_island<AP, TRACKED>(p, isl0 + k, tout, sout, ct, cs);
+  }
+}
+
+template <int AP, bool TRACKED, bool T2>
 __global__ void __launch_bounds__(kStreamThreads)
     step_streamed_kernel(RunParams p, Deposit dep, uint32_t G, int do_mig,
                          const uint32_t *__restrict__ tin, const uint64_t *__restrict__ sin,
                          uint32_t *__restrict__ tout, uint64_t *__restrict__ sout) {
-  const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
-  for (uint32_t isl = blockIdx.x * wpb + (threadIdx.x >> 5); isl < p.islands; isl += nwarps) {
-    const size_t base = (size_t)isl * p.n;
-    uint32_t pt[AP];
-    uint64_t ps[AP];
-#pragma unroll
-    for (int a = 0; a < AP; ++a) {
-      const uint32_t j = lane + 32u * a;
-      pt[a] = 0;
-      ps[a] = 0;
-      if (j < p.n) {
-        pt[a] = __ldcs(tin + base + j);
-        if constexpr (TRACKED) ps[a] = __ldcs(sin + base + j);
-      }
-    }
-    Words4 w[AP];
-    replication_words<AP>(p, isl, G, w);
-    if (do_mig) immigrate_from_planes<AP, TRACKED>(p, isl, G, tin, sin, pt, ps);
-    uint32_t ct[AP];
-    uint64_t cs[AP];
-    replicate<AP, TRACKED>(p, dep, isl, G, w, pt, ps, ct, cs);
-#pragma unroll
-    for (int a = 0; a < AP; ++a) {
-      const uint32_t j = lane + 32u * a;
-      if (j < p.n) {
-        __stcs(tout + base + j, ct[a]);
-        if constexpr (TRACKED) __stcs(sout + base + j, cs[a]);
-      }
-    }
+  const uint32_t ngroups = (p.islands + kGroup - 1) / kGroup;
+  for (uint32_t grp = blockIdx.x * wpb + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
+    const uint32_t isl0 = grp * kGroup;
+    if (isl0 + kGroup <= p.islands)
+      full_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
+    else
+      partial_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
   }
 }
 
-template <int AP, bool TRACKED>
+template <int AP, bool TRACKED, bool T2>
 static int streamed_blocks() {
   static int blocks = 0;
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_streamed_kernel<AP, TRACKED>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_streamed_kernel<AP, TRACKED, T2>,
                                                   kStreamThreads, 0);
     blocks = sms * (per_sm > 0 ? per_sm : 1);
   }
   return blocks;
+}
+
+template <int AP, bool TRACKED, bool T2>
+static void launch_streamed_t(const RunParams &p, const Deposit &dep, uint32_t G, bool do_mig,
+                              const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
+                              uint64_t *sout, cudaStream_t stream) {
+  const uint32_t groups = (p.islands + kGroup - 1) / kGroup;
+  const uint32_t need = (groups + kStreamThreads / 32 - 1) / (kStreamThreads / 32);
+  int b = streamed_blocks<AP, TRACKED, T2>();
+  if ((uint32_t)b > need) b = (int)need;
+  step_streamed_kernel<AP, TRACKED, T2>
+      <<<b, kStreamThreads, 0, stream>>>(p, dep, G, do_mig ? 1 : 0, tin, sin, tout, sout);
 }
 
 cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
@@ -108,18 +233,21 @@ cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
                                  uint64_t *sout, cudaStream_t stream) {
   const Deposit dep = deposit_for(p, G);
   const bool tracked = p.policy != HSGA_NONE;
-  const uint32_t need = (p.islands + kStreamThreads / 32 - 1) / (kStreamThreads / 32);
-#define HSGA_LAUNCH(AP_, TR_)                                                              \
-  {                                                                                       \
-    int b = streamed_blocks<AP_, TR_>();                                                  \
-    if ((uint32_t)b > need) b = (int)need;                                                \
-    step_streamed_kernel<AP_, TR_><<<b, kStreamThreads, 0, stream>>>(p, dep, G, do_mig,   \
-                                                                     tin, sin, tout, sout); \
-  }
+  const bool t2 = p.tournament == 2;
+#define HSGA_LAUNCH(AP_, TR_, T2_) \
+  launch_streamed_t<AP_, TR_, T2_>(p, dep, G, do_mig, tin, sin, tout, sout, stream)
   if (p.n <= 32) {
-    if (tracked) HSGA_LAUNCH(1, true) else HSGA_LAUNCH(1, false)
+    if (tracked) {
+      if (t2) HSGA_LAUNCH(1, true, true); else HSGA_LAUNCH(1, true, false);
+    } else {
+      if (t2) HSGA_LAUNCH(1, false, true); else HSGA_LAUNCH(1, false, false);
+    }
   } else {
-    if (tracked) HSGA_LAUNCH(2, true) else HSGA_LAUNCH(2, false)
+    if (tracked) {
+      if (t2) HSGA_LAUNCH(2, true, true); else HSGA_LAUNCH(2, true, false);
+    } else {
+      if (t2) HSGA_LAUNCH(2, false, true); else HSGA_LAUNCH(2, false, false);
+    }
   }
 #undef HSGA_LAUNCH
   return cudaGetLastError();
@@ -133,7 +261,7 @@ __global__ void emigrate_kernel(RunParams p, uint32_t G, const uint32_t *__restr
                                 const uint64_t *__restrict__ s, uint4 *__restrict__ rec) {
   const uint32_t isl = blockIdx.x * blockDim.x + threadIdx.x;
   if (isl >= p.islands) return;
-  const Words4 m = philox(p.k0, p.k1, kSlotEmigrant, isl, G, kPurposeMigration);
+  const Words4 m = philox_rk(p, kSlotEmigrant, isl, G, kPurposeMigration);
   const size_t a = (size_t)isl * p.n + uindex(m.x, p.n);
   const uint64_t sv = s ? s[a] : 0ull;
   rec[isl] = make_uint4(t[a], (uint32_t)sv, (uint32_t)(sv >> 32), m.y >> 30);
@@ -143,7 +271,7 @@ __global__ void immigrate_kernel(RunParams p, uint32_t G, uint32_t *__restrict__
                                  uint64_t *__restrict__ s, const uint4 *__restrict__ rec) {
   const uint32_t isl = blockIdx.x * blockDim.x + threadIdx.x;
   if (isl >= p.islands) return;
-  const Words4 v = philox(p.k0, p.k1, kSlotImmigrant, isl, G, kPurposeMigration);
+  const Words4 v = philox_rk(p, kSlotImmigrant, isl, G, kPurposeMigration);
   const uint32_t place[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
   for (uint32_t d = 0; d < 4; ++d) {
@@ -199,7 +327,7 @@ __global__ void __launch_bounds__(1024)
   const uint32_t I = p.islands;
   for (uint32_t j = threadIdx.x; j < K2; j += blockDim.x) {
     if (j < k) {
-      const Words4 w = philox(p.k0, p.k1, j, 0xFFFFFFFFu, G, kPurposeSampleDraw);
+      const Words4 w = philox_rk(p, j, 0xFFFFFFFFu, G, kPurposeSampleDraw);
       const uint32_t r = j + uindex(w.x, I - j);
       draw[j] = r;
       pairs[j] = ((unsigned long long)r << 32) | j;
@@ -247,7 +375,7 @@ __global__ void __launch_bounds__(1024)
   for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
     const int last = last_before(pairs, K2, draw[j], j);
     const uint32_t island = last < 0 ? draw[j] : (uint32_t)val[last];
-    const Words4 w = philox(p.k0, p.k1, kSlotSample, island, G, kPurposeMigration);
+    const Words4 w = philox_rk(p, kSlotSample, island, G, kPurposeMigration);
     const uint32_t slot = uindex(w.x, p.n);
     const size_t a = (size_t)island * p.n + slot;
     const uint64_t sv = s ? s[a] : 0ull;
@@ -266,7 +394,7 @@ __global__ void iota_kernel(uint32_t *perm, uint32_t I) {
 __global__ void shuffle_serial_kernel(RunParams p, uint32_t G, uint32_t k, uint32_t *perm) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (uint32_t j = 0; j < k; ++j) {
-    const Words4 w = philox(p.k0, p.k1, j, 0xFFFFFFFFu, G, kPurposeSampleDraw);
+    const Words4 w = philox_rk(p, j, 0xFFFFFFFFu, G, kPurposeSampleDraw);
     const uint32_t r = j + uindex(w.x, p.islands - j);
     const uint32_t a = perm[j], b = perm[r];
     perm[j] = b;
@@ -281,7 +409,7 @@ __global__ void gather_samples_kernel(RunParams p, uint32_t G, uint32_t k, const
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
   const uint32_t island = perm[j];
-  const Words4 w = philox(p.k0, p.k1, kSlotSample, island, G, kPurposeMigration);
+  const Words4 w = philox_rk(p, kSlotSample, island, G, kPurposeMigration);
   const uint32_t slot = uindex(w.x, p.n);
   const size_t a = (size_t)island * p.n + slot;
   const uint64_t sv = s ? s[a] : 0ull;

@@ -87,24 +87,24 @@ __global__ void __launch_bounds__(kResidentThreads)
     // generation G0+g0+o, lane 16+o its placement block; every lane holds
     // the deposit of generation G0+g0+(lane & 15), packed as site*b | on<<8.
     const uint32_t Gl = G0 + g0 + (lane & (kChunk - 1));
-    const Deposit dl = deposit_for(p, Gl);
-    const uint32_t dpack = dl.on ? (dl.shift | 0x100u) : 0u;
+    uint32_t dpack = 0u;
+    if (p.policy != HSGA_NONE) {
+      const uint32_t site = site_of(p.policy, p.S, p.W, Gl);
+      if (site < p.S) dpack = (site * p.bits) | 0x100u;
+    }
     Words4 mig[IPW];
 #pragma unroll
     for (int k = 0; k < IPW; ++k) {
       mig[k] = Words4{0, 0, 0, 0};
       if (any_mig && isl[k] < p.islands)
-        mig[k] = philox(p.k0, p.k1, lane < kChunk ? kSlotEmigrant : kSlotImmigrant, isl[k], Gl,
+        mig[k] = philox_rk(p, lane < kChunk ? kSlotEmigrant : kSlotImmigrant, isl[k], Gl,
                         kPurposeMigration);
     }
     const uint32_t steps = min(kChunk, ngen - g0);
     for (uint32_t o = 0; o < steps; ++o) {
       const uint32_t G = G0 + g0 + o;
       const uint32_t dp = __shfl_sync(kFull, dpack, o);
-      Deposit dep;
-      dep.on = dp >> 8;
-      dep.shift = dp & 0xFFu;
-      dep.clear = ~(p.vmask << dep.shift);
+      const Deposit dep = deposit_from_bit(dp >> 8, dp & 0xFFu, (uint32_t)p.vmask);
       const bool do_mig = migrates(p, G) && !(premigrated && g0 + o == 0);
       uint32_t buf = 0, seq = 0;
       if (do_mig) {
