@@ -63,6 +63,37 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",
+                  "paper_2404_10861_gb300/csrc/hsga_island.cuh",
+                  "paper_2404_10861_gb300/csrc/hsga_kernels.cu"]
+PROFILE = os.path.join(ROOT, "profiles", "step_streamed_wafer.md")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the streamed kernel from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    try:
+        fields = {}
+        for line in open(PROFILE):
+            if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch")):
+                k, v = line.strip().strip("`").split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_sha256") != kernel_source_hash():
+            return None
+        return int(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -253,13 +284,7 @@ def run_ours(args):
     per_launch_s = gen_ms / 1e3 / (GENS_PER_STEP * args.steps)
     achieved = BYTES_PER_LAUNCH / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "step_streamed_wafer_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
 
     # end to end through the C-ABI with host buffers: host->device population,
     # generations, device->host sample, every step

@@ -93,36 +93,39 @@ __device__ __forceinline__ void group_land(const GroupMigration &gm, uint32_t k,
   }
 }
 
-template <int AP, bool TRACKED>
+// NN: agents per island known at compile time (32), or 0 for a runtime n.
+template <int AP, bool TRACKED, int NN = 0>
 __device__ __forceinline__ void load_island(const RunParams &p, uint32_t isl,
                                             const uint32_t *__restrict__ tin,
                                             const uint64_t *__restrict__ sin, uint32_t (&t)[AP],
                                             uint64_t (&s)[AP]) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t base = isl * p.n;
+  const uint32_t n = NN ? (uint32_t)NN : p.n;
+  const uint32_t base = isl * n;
 #pragma unroll
   for (int a = 0; a < AP; ++a) {
     const uint32_t j = lane + 32u * a;
     t[a] = 0;
     s[a] = 0;
-    if (j < p.n) {
+    if (NN == 32 || j < n) {
       t[a] = __ldcs(tin + base + j);
       if constexpr (TRACKED) s[a] = __ldcs(sin + base + j);
     }
   }
 }
 
-template <int AP, bool TRACKED>
+template <int AP, bool TRACKED, int NN = 0>
 __device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
                                              uint32_t *__restrict__ tout,
                                              uint64_t *__restrict__ sout,
                                              const uint32_t (&t)[AP], const uint64_t (&s)[AP]) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t base = isl * p.n;
+  const uint32_t n = NN ? (uint32_t)NN : p.n;
+  const uint32_t base = isl * n;
 #pragma unroll
   for (int a = 0; a < AP; ++a) {
     const uint32_t j = lane + 32u * a;
-    if (j < p.n) {
+    if (NN == 32 || j < n) {
       __stcs(tout + base + j, t[a]);
       if constexpr (TRACKED) __stcs(sout + base + j, s[a]);
     }
@@ -130,36 +133,44 @@ __device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
 }
 
 // One full group: all six islands' genomes are requested up front (deep
-// memory-level parallelism), then the islands are processed in pairs so that
-// each lane runs two independent Philox chains.
-template <int AP, bool TRACKED, bool T2>
+// memory-level parallelism), then the islands are processed ILV at a time so
+// that each lane runs ILV independent Philox chains (instruction-level
+// parallelism hides the multiply-xor dependency chain of the rounds).
+constexpr int kInterleave = 2;
+
+template <int AP, bool TRACKED, bool T2, int NN, int ILV = kInterleave>
 __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &dep, uint32_t G,
                                            bool do_mig, uint32_t isl0,
                                            const uint32_t *__restrict__ tin,
                                            const uint64_t *__restrict__ sin,
                                            uint32_t *__restrict__ tout,
                                            uint64_t *__restrict__ sout) {
+  static_assert(kGroup % ILV == 0, "interleave width must divide the group");
   uint32_t pt[kGroup][AP];
   uint64_t ps[kGroup][AP];
 #pragma unroll
-  for (uint32_t k = 0; k < kGroup; ++k) load_island<AP, TRACKED>(p, isl0 + k, tin, sin, pt[k], ps[k]);
+  for (uint32_t k = 0; k < kGroup; ++k)
+    load_island<AP, TRACKED, NN>(p, isl0 + k, tin, sin, pt[k], ps[k]);
   GroupMigration gm;
   if (do_mig) group_migration<TRACKED>(p, isl0, G, tin, sin, gm);
 #pragma unroll
-  for (uint32_t k = 0; k < kGroup; k += 2) {
-    Words4 wa[AP], wb[AP];
-    replication_words<AP>(p, isl0 + k, G, wa);
-    replication_words<AP>(p, isl0 + k + 1, G, wb);
+  for (uint32_t k = 0; k < kGroup; k += ILV) {
+    Words4 w[ILV][AP];
+#pragma unroll
+    for (int i = 0; i < ILV; ++i) replication_words<AP>(p, isl0 + k + i, G, w[i]);
     if (do_mig) {
-      group_land<AP, TRACKED>(gm, k, pt[k], ps[k]);
-      group_land<AP, TRACKED>(gm, k + 1, pt[k + 1], ps[k + 1]);
+#pragma unroll
+      for (int i = 0; i < ILV; ++i) group_land<AP, TRACKED>(gm, k + i, pt[k + i], ps[k + i]);
     }
-    uint32_t ct[2][AP];
-    uint64_t cs[2][AP];
-    replicate<AP, TRACKED, T2>(p, dep, isl0 + k, G, wa, pt[k], ps[k], ct[0], cs[0]);
-    replicate<AP, TRACKED, T2>(p, dep, isl0 + k + 1, G, wb, pt[k + 1], ps[k + 1], ct[1], cs[1]);
-    store_island<AP, TRACKED>(p, isl0 + k, tout, sout, ct[0], cs[0]);
-    store_island<AP, TRACKED>(p, isl0 + k + 1, tout, sout, ct[1], cs[1]);
+    uint32_t ct[ILV][AP];
+    uint64_t cs[ILV][AP];
+#pragma unroll
+    for (int i = 0; i < ILV; ++i)
+      replicate<AP, TRACKED, T2>(p, dep, isl0 + k + i, G, w[i], pt[k + i], ps[k + i], ct[i],
+                                 cs[i]);
+#pragma unroll
+    for (int i = 0; i < ILV; ++i)
+      store_island<AP, TRACKED, NN>(p, isl0 + k + i, tout, sout, ct[i], cs[i]);
   }
 }
 
@@ -185,7 +196,7 @@ __device__ __noinline__ void partial_group(const RunParams &p, const Deposit &de
   }
 }
 
-template <int AP, bool TRACKED, bool T2>
+template <int AP, bool TRACKED, bool T2, int NN>
 __global__ void __launch_bounds__(kStreamThreads)
     step_streamed_kernel(RunParams p, Deposit dep, uint32_t G, int do_mig,
                          const uint32_t *__restrict__ tin, const uint64_t *__restrict__ sin,
@@ -196,35 +207,35 @@ __global__ void __launch_bounds__(kStreamThreads)
   for (uint32_t grp = blockIdx.x * wpb + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
     const uint32_t isl0 = grp * kGroup;
     if (isl0 + kGroup <= p.islands)
-      full_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
+      full_group<AP, TRACKED, T2, NN>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
     else
       partial_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
   }
 }
 
-template <int AP, bool TRACKED, bool T2>
+template <int AP, bool TRACKED, bool T2, int NN>
 static int streamed_blocks() {
   static int blocks = 0;
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_streamed_kernel<AP, TRACKED, T2>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_streamed_kernel<AP, TRACKED, T2, NN>,
                                                   kStreamThreads, 0);
     blocks = sms * (per_sm > 0 ? per_sm : 1);
   }
   return blocks;
 }
 
-template <int AP, bool TRACKED, bool T2>
+template <int AP, bool TRACKED, bool T2, int NN>
 static void launch_streamed_t(const RunParams &p, const Deposit &dep, uint32_t G, bool do_mig,
                               const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
                               uint64_t *sout, cudaStream_t stream) {
   const uint32_t groups = (p.islands + kGroup - 1) / kGroup;
   const uint32_t need = (groups + kStreamThreads / 32 - 1) / (kStreamThreads / 32);
-  int b = streamed_blocks<AP, TRACKED, T2>();
+  int b = streamed_blocks<AP, TRACKED, T2, NN>();
   if ((uint32_t)b > need) b = (int)need;
-  step_streamed_kernel<AP, TRACKED, T2>
+  step_streamed_kernel<AP, TRACKED, T2, NN>
       <<<b, kStreamThreads, 0, stream>>>(p, dep, G, do_mig ? 1 : 0, tin, sin, tout, sout);
 }
 
@@ -234,21 +245,24 @@ cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
   const Deposit dep = deposit_for(p, G);
   const bool tracked = p.policy != HSGA_NONE;
   const bool t2 = p.tournament == 2;
-#define HSGA_LAUNCH(AP_, TR_, T2_) \
-  launch_streamed_t<AP_, TR_, T2_>(p, dep, G, do_mig, tin, sin, tout, sout, stream)
-  if (p.n <= 32) {
-    if (tracked) {
-      if (t2) HSGA_LAUNCH(1, true, true); else HSGA_LAUNCH(1, true, false);
-    } else {
-      if (t2) HSGA_LAUNCH(1, false, true); else HSGA_LAUNCH(1, false, false);
-    }
-  } else {
-    if (tracked) {
-      if (t2) HSGA_LAUNCH(2, true, true); else HSGA_LAUNCH(2, true, false);
-    } else {
-      if (t2) HSGA_LAUNCH(2, false, true); else HSGA_LAUNCH(2, false, false);
-    }
+#define HSGA_LAUNCH(AP_, TR_, T2_, NN_) \
+  launch_streamed_t<AP_, TR_, T2_, NN_>(p, dep, G, do_mig, tin, sin, tout, sout, stream)
+#define HSGA_LAUNCH_T(AP_, NN_)                         \
+  if (tracked) {                                        \
+    if (t2) HSGA_LAUNCH(AP_, true, true, NN_);          \
+    else HSGA_LAUNCH(AP_, true, false, NN_);            \
+  } else {                                              \
+    if (t2) HSGA_LAUNCH(AP_, false, true, NN_);         \
+    else HSGA_LAUNCH(AP_, false, false, NN_);           \
   }
+  if (p.n == 32) {
+    HSGA_LAUNCH_T(1, 32)
+  } else if (p.n < 32) {
+    HSGA_LAUNCH_T(1, 0)
+  } else {
+    HSGA_LAUNCH_T(2, 0)
+  }
+#undef HSGA_LAUNCH_T
 #undef HSGA_LAUNCH
   return cudaGetLastError();
 }
