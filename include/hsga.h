@@ -204,6 +204,30 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
+/* Allocation-free variant of hsga_run_generations for callers that must not
+ * allocate device memory (a process under a fixed memory budget, a plugin
+ * living inside another framework's allocator): it advances n_generations
+ * synchronous generations (steps a1-a6 each, bit-identical to a grid run
+ * with the same configuration) in place on the caller's device planes, with
+ * the resident kernel, and performs no device allocation of any kind.  The
+ * paper has no counterpart; it is an interface convenience of this library.
+ *   cfg: run configuration (cfg->kernel is ignored); rows*cols <= 8192
+ *        islands, else HSGA_ERR_INVALID_ARG.
+ *   generation: G of the population on entry (the result is at G + n).
+ *   trait, surf: device planes, layout as hsga_set_population; surf may be
+ *        NULL only for HSGA_NONE.  Host pointers are HSGA_ERR_INVALID_ARG.
+ * Scratch (migrant records, sequence flags, error word: ~288 KiB) is one
+ * array built into the library and held on every device that loads it until
+ * exit.  The first call on a device looks its address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU race.  The
+ * call is stream-ordered on cuda_stream and waits for it before returning the
+ * kernels' status (HSGA_ERR_WAIT_TIMEOUT / HSGA_ERR_DEVICE on a device-side
+ * error). */
+int hsga_run_generations_noalloc(const hsga_config *cfg, uint64_t generation,
+                                 uint64_t n_generations, uint32_t *trait,
+                                 uint64_t *surf, void *cuda_stream);
+
 const char *hsga_status_string(int status);
 
 /* ABI version (major * 100 + minor). */

@@ -79,6 +79,9 @@ _SIGS = {
                      ctypes.c_void_p], ctypes.c_int),
     "hsga_sites_device": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hsga_run_generations_noalloc": ([ctypes.POINTER(hsga_config), ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p], ctypes.c_int),
 }
 
 _lib = None
@@ -231,6 +234,16 @@ def hsga_sites_device(policy: int, S: int, W: int, T0: int, count: int, out_dev,
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(lib().hsga_sites_device(policy, S, W, T0, count, _ptr(out_dev), s),
            "hsga_sites_device")
+
+
+def hsga_run_generations_noalloc(cfg: hsga_config, generation: int, n: int, trait_dev,
+                                 surf_dev, stream=None):
+    """Advances device planes in place without any device allocation (the
+    library's built-in scratch is used; see include/hsga.h)."""
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().hsga_run_generations_noalloc(ctypes.byref(cfg), int(generation), int(n),
+                                              _ptr(trait_dev), _ptr(surf_dev), s),
+           "hsga_run_generations_noalloc")
 
 
 # ----------------------------------------------------------- convenience ---

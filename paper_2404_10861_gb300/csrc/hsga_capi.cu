@@ -539,3 +539,10 @@ int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint
 }
 
 }  // extern "C"
+
+// Configuration checks and kernel parameters, shared with the
+// allocation-free entry point (hsga_noalloc.cu).
+namespace hsga {
+int validate_config(const hsga_config *c) { return validate(c); }
+RunParams params_from_config(const hsga_config *c) { return make_params(c); }
+}  // namespace hsga

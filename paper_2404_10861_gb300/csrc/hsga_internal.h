@@ -43,6 +43,10 @@ cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint
                           const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
                           uint32_t *scratch, cudaStream_t stream);
 
+// Configuration checks and kernel parameters (defined in hsga_capi.cu).
+int validate_config(const hsga_config *c);
+RunParams params_from_config(const hsga_config *c);
+
 cudaError_t launch_sites(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
                          uint32_t *out, cudaStream_t stream);
 
