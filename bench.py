@@ -336,6 +336,124 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+SECONDARY = {
+    # the 4x4-island tiny workload (whole 2,000-generation run per step) and the
+    # 64x64-island mid-grid workload (1,000 generations per step); both run on
+    # the default kernel choice (resident: genomes stay in registers)
+    "tiny": (dict(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2,
+                  interval=1, p_ben=0.0, p_del=0.0), 2000),
+    "mid": (dict(rows=64, cols=64, n=32, tournament=2, policy="tilted", bits=2, W=2,
+                 interval=1, p_ben=1e-3, p_del=0.0), 1000),
+}
+
+
+def run_secondary(args):
+    """Informational lines for the smaller workloads (not the headline)."""
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb
+    _build.build()
+    torch.cuda.set_device(0)
+    kw, gens = SECONDARY[args.workload]
+    agents = kw["rows"] * kw["cols"] * kw["n"]
+    out = []
+    for kernel in (hb.KERNEL_RESIDENT, hb.KERNEL_RESIDENT_GRID, hb.KERNEL_STREAMED):
+        stream = torch.cuda.Stream()
+        with hb.Grid(stream=stream.cuda_stream, kernel=kernel, seed=1, **kw) as g:
+            for _ in range(args.warmup):
+                g.run(gens)
+            g.sync()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.steps):
+                g.run(gens)
+            s1.record(stream)
+            g.sync()
+            ms = s0.elapsed_time(s1)
+            st = g.stats()
+        out.append({"kernel": {hb.KERNEL_RESIDENT: "resident", hb.KERNEL_RESIDENT_GRID:
+                               "resident_grid", hb.KERNEL_STREAMED: "streamed"}[kernel],
+                    "value": agents * gens * args.steps / (ms / 1e3),
+                    "ms_per_step": ms / args.steps, "us_per_generation": ms * 1e3 / (gens * args.steps),
+                    "islands_per_warp": st["islands_per_warp"], "blocks": st["blocks"]})
+    print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
+                      "workload": args.workload, "config": dict(kw, generations_per_step=gens),
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "u32",
+                      "data": "synthetic", "kernels": out}), flush=True)
+
+
+def splitmix64(x: int) -> int:
+    """Seed derivation hash(master, index) (SplitMix64 finaliser, Steele et al. 2014)."""
+    x = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return x ^ (x >> 31)
+
+
+def batched_runs(gen_scale: int, count: int = 256, master: int = 4):
+    """The batched-replicates workload: grid side uniform over
+    {8,16,32,64,128,256}, square or 2:1 (coin flip), 16-64 agents per island,
+    steady / tilted / stretched, adaptation on (p_ben 1e-3) or off, budgets
+    uniform over [10,000, 200,000] generations divided by gen_scale."""
+    rng = np.random.default_rng(master)
+    runs = []
+    for i in range(count):
+        side = int(rng.choice([8, 16, 32, 64, 128, 256]))
+        rows, cols = (side, side) if rng.random() < 0.5 else (side, 2 * side)
+        n = int(rng.integers(16, 65))
+        policy = str(rng.choice(["steady", "tilted", "stretched"]))
+        p_ben = 1e-3 if rng.random() < 0.5 else 0.0
+        gens = int(rng.integers(10_000, 200_001)) // gen_scale
+        runs.append((gens, dict(rows=rows, cols=cols, n=n, tournament=2, policy=policy,
+                                bits=1, W=2, interval=1, p_ben=p_ben, p_del=0.0,
+                                seed=splitmix64((master << 32) | i))))
+    return runs
+
+
+def run_batched(args):
+    """Batched replicates in one batch against the same runs launched one
+    after another through the plain grid API."""
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb
+    _build.build()
+    torch.cuda.set_device(0)
+    hb.use_torch_allocator()
+    runs = batched_runs(args.gen_scale)
+    reps = sum(g * kw["rows"] * kw["cols"] * kw["n"] for g, kw in runs)
+    stream = torch.cuda.Stream()
+    # batched: all runs admitted at tick 0, run until every budget is spent
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with hb.Batch(stream=stream.cuda_stream) as b:
+        for g, kw in runs:
+            b.add(g, **kw)
+        b.run(10**9)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        st = b.stats()
+    # plain: one grid per run, one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, kw in runs:
+        with hb.Grid(stream=stream.cuda_stream, **kw) as grid:
+            grid.run(g)
+            grid.sync()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "runs/hour and agent replications/sec, batched vs plain",
+        "workload": "batched replicates: 256 runs, sides {8..256} square or 2:1, 16-64 agents "
+                    "per island, steady/tilted/stretched, adaptive coin flip, master seed 4",
+        "generation_budgets": f"uniform [10000, 200000] / {args.gen_scale}",
+        "replications": reps,
+        "batched": {"seconds": t_batch, "runs_per_hour": len(runs) * 3600 / t_batch,
+                    "agent_replications_per_s": reps / t_batch, "phases": st["phases"],
+                    "kernel_launches": st["kernel_launches"],
+                    "threads_per_block": st["threads_per_block"]},
+        "plain_sequential": {"seconds": t_plain, "runs_per_hour": len(runs) * 3600 / t_plain,
+                             "agent_replications_per_s": reps / t_plain},
+        "speedup": t_plain / t_batch, "dtype": "u32", "data": "synthetic"}), flush=True)
+
+
 def run_profile(gens: int):
     """Workload only, for profilers: founders, `gens` generations, one sample."""
     import torch
@@ -360,7 +478,19 @@ def main():
     ap.add_argument("--profile-gens", type=int, default=0,
                     help="profiling mode: only run this many generations of the workload "
                          "(no timing); used for ncu captures")
+    ap.add_argument("--workload", default="wafer", choices=["wafer", "tiny", "mid", "batched"],
+                    help="wafer: the benchmark line; tiny / mid / batched: informational lines")
+    ap.add_argument("--gen-scale", type=int, default=100,
+                    help="batched workload: divide the generation budgets by this")
     args = ap.parse_args()
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload != "wafer":
+        if args.warmup < 3:
+            args.warmup = 3
+        run_secondary(args)
+        return
     if args.profile_gens:
         run_profile(args.profile_gens)
         return

@@ -84,7 +84,10 @@ typedef enum hsga_policy {
 typedef enum hsga_kernel {
   HSGA_KERNEL_AUTO = 0,      /* resident when the grid fits on chip, else streamed */
   HSGA_KERNEL_STREAMED = 1,  /* one launch per generation, population in HBM */
-  HSGA_KERNEL_RESIDENT = 2   /* persistent cooperative launch, genomes in registers */
+  HSGA_KERNEL_RESIDENT = 2,  /* persistent launch, genomes in registers; grids of at
+                                most 32 warps run in one block (block barriers), larger
+                                ones as a cooperative grid (neighbour flags) */
+  HSGA_KERNEL_RESIDENT_GRID = 3  /* resident, always the cooperative multi-block form */
 } hsga_kernel;
 
 /* Run configuration (plain data, caller-owned; copied by hsga_init_grid). */
@@ -203,6 +206,74 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
  * CPU"). */
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
+
+/* ------------------------------------------------------------ batches ---
+ * Many independent runs (uneven grids, agents per island, policies,
+ * mutation rates, seeds and generation budgets) advanced together: each
+ * "tick" advances every active run by one generation in one launch per
+ * agents-per-lane class (n <= 32, n > 32), ticks are replayed from CUDA
+ * graphs, and the launch shape is picked by timing real ticks.  Every run
+ * is bit-identical to the same configuration run alone on a grid.  Runs can
+ * be added and removed between calls (continuous batching); a run added at
+ * tick t starts from founders at generation 0 and is active for its budget
+ * of ticks.  Paper: many replicate runs of the island-model GA (section
+ * "On-hardware Trial": replicates per treatment and array size). */
+typedef struct hsga_batch hsga_batch;
+
+typedef struct hsga_batch_run_info {
+  uint64_t generation;  /* generations the run has completed */
+  uint64_t budget;      /* generations it was admitted for */
+  uint64_t agents;
+  uint32_t done;        /* generation == budget */
+  uint32_t live;        /* planes still held (not removed) */
+} hsga_batch_run_info;
+
+typedef struct hsga_batch_stats {
+  uint64_t tick;             /* ticks elapsed */
+  uint64_t replications;     /* agent replications advanced */
+  uint64_t kernel_launches;
+  uint64_t phases;           /* distinct active sets run */
+  uint64_t device_bytes;     /* population planes held */
+  uint32_t live_runs, active_runs;
+  uint32_t threads_per_block, blocks;  /* current launch shape */
+} hsga_batch_stats;
+
+/* Creates an empty batch at tick 0.  cuda_stream: a cudaStream_t; NULL makes
+ * the batch create (and later destroy) its own non-blocking stream, because
+ * graphs cannot be captured on the legacy default stream. */
+int hsga_batch_create(void *cuda_stream, hsga_batch **out);
+
+/* Admits a run (founders at generation 0) for `generations` generations;
+ * allocates its two population planes (24 bytes per agent) through the
+ * registered allocator.  *run_id receives its index. */
+int hsga_batch_add(hsga_batch *b, const hsga_config *cfg, uint64_t generations,
+                   uint32_t *run_id);
+
+/* Advances the batch by up to `ticks` ticks (stops early once no run is
+ * active; each run stops at its own budget).  Stream-ordered. */
+int hsga_batch_run(hsga_batch *b, uint64_t ticks);
+
+int hsga_batch_info(const hsga_batch *b, uint32_t run, hsga_batch_run_info *out);
+
+/* Population of a live run at its current generation (layout as
+ * hsga_get_population; host or device destinations).  Synchronous. */
+int hsga_batch_get_population(hsga_batch *b, uint32_t run, uint32_t *trait, uint64_t *surf);
+
+/* Step a7 on a live run at its current generation (same draws and layout as
+ * hsga_sample_surfaces).  Synchronous. */
+int hsga_batch_sample(hsga_batch *b, uint32_t run, uint32_t k, uint32_t *out_words,
+                      uint32_t *out_island_slot);
+
+/* Frees a run's planes (its id stays allocated; further queries fail). */
+int hsga_batch_remove(hsga_batch *b, uint32_t run);
+
+int hsga_batch_get_stats(const hsga_batch *b, hsga_batch_stats *out);
+
+/* Device bytes a run of this configuration holds in a batch (admission by
+ * memory footprint).  Host function. */
+int hsga_run_footprint(const hsga_config *cfg, uint64_t *bytes);
+
+void hsga_batch_destroy(hsga_batch *b);
 
 /* Allocation-free variant of hsga_run_generations for callers that must not
  * allocate device memory (a process under a fixed memory budget, a plugin

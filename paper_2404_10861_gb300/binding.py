@@ -20,7 +20,7 @@ from . import _build
 STEADY, TILTED, STRETCHED, TRIVIAL, NONE = 0, 1, 2, 3, 4
 POLICIES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
             "trivial": TRIVIAL, "none": NONE}
-KERNEL_AUTO, KERNEL_STREAMED, KERNEL_RESIDENT = 0, 1, 2
+KERNEL_AUTO, KERNEL_STREAMED, KERNEL_RESIDENT, KERNEL_RESIDENT_GRID = 0, 1, 2, 3
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed",
           -3: "CUDA runtime error", -4: "kernel reported an inconsistent state",
@@ -47,6 +47,19 @@ class hsga_stats(ctypes.Structure):
     _fields_ = [("generation", ctypes.c_uint64), ("replications", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
                 ("islands_per_warp", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32)]
+
+
+class hsga_batch_run_info(ctypes.Structure):
+    _fields_ = [("generation", ctypes.c_uint64), ("budget", ctypes.c_uint64),
+                ("agents", ctypes.c_uint64), ("done", ctypes.c_uint32), ("live", ctypes.c_uint32)]
+
+
+class hsga_batch_stats(ctypes.Structure):
+    _fields_ = [("tick", ctypes.c_uint64), ("replications", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("phases", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("live_runs", ctypes.c_uint32),
+                ("active_runs", ctypes.c_uint32), ("threads_per_block", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32)]
 
 
@@ -79,6 +92,21 @@ _SIGS = {
                      ctypes.c_void_p], ctypes.c_int),
     "hsga_sites_device": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hsga_batch_create": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "hsga_batch_add": ([ctypes.c_void_p, ctypes.POINTER(hsga_config), ctypes.c_uint64,
+                        ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "hsga_batch_run": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "hsga_batch_info": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(hsga_batch_run_info)],
+                        ctypes.c_int),
+    "hsga_batch_get_population": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                   ctypes.c_void_p], ctypes.c_int),
+    "hsga_batch_sample": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                           ctypes.c_void_p], ctypes.c_int),
+    "hsga_batch_remove": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "hsga_batch_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_batch_stats)], ctypes.c_int),
+    "hsga_run_footprint": ([ctypes.POINTER(hsga_config), ctypes.POINTER(ctypes.c_uint64)],
+                           ctypes.c_int),
+    "hsga_batch_destroy": ([ctypes.c_void_p], None),
     "hsga_run_generations_noalloc": ([ctypes.POINTER(hsga_config), ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p], ctypes.c_int),
@@ -244,6 +272,118 @@ def hsga_run_generations_noalloc(cfg: hsga_config, generation: int, n: int, trai
     _check(lib().hsga_run_generations_noalloc(ctypes.byref(cfg), int(generation), int(n),
                                               _ptr(trait_dev), _ptr(surf_dev), s),
            "hsga_run_generations_noalloc")
+
+
+def hsga_batch_create(cuda_stream=None):
+    out = ctypes.c_void_p()
+    s = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+    _check(lib().hsga_batch_create(s, ctypes.byref(out)), "hsga_batch_create")
+    return out
+
+
+def hsga_batch_add(b, cfg: hsga_config, generations: int) -> int:
+    rid = ctypes.c_uint32()
+    _check(lib().hsga_batch_add(b, ctypes.byref(cfg), int(generations), ctypes.byref(rid)),
+           "hsga_batch_add")
+    return rid.value
+
+
+def hsga_batch_run(b, ticks: int):
+    _check(lib().hsga_batch_run(b, int(ticks)), "hsga_batch_run")
+
+
+def hsga_batch_info(b, run: int) -> dict:
+    info = hsga_batch_run_info()
+    _check(lib().hsga_batch_info(b, run, ctypes.byref(info)), "hsga_batch_info")
+    return {f: getattr(info, f) for f, _ in hsga_batch_run_info._fields_}
+
+
+def hsga_batch_get_population(b, run: int, trait, surf):
+    _check(lib().hsga_batch_get_population(b, run, _ptr(trait), _ptr(surf)),
+           "hsga_batch_get_population")
+
+
+def hsga_batch_sample(b, run: int, k: int, out_words, out_island_slot=None):
+    _check(lib().hsga_batch_sample(b, run, int(k), _ptr(out_words), _ptr(out_island_slot)),
+           "hsga_batch_sample")
+
+
+def hsga_batch_remove(b, run: int):
+    _check(lib().hsga_batch_remove(b, run), "hsga_batch_remove")
+
+
+def hsga_batch_get_stats(b) -> dict:
+    st = hsga_batch_stats()
+    _check(lib().hsga_batch_get_stats(b, ctypes.byref(st)), "hsga_batch_get_stats")
+    return {f: getattr(st, f) for f, _ in hsga_batch_stats._fields_}
+
+
+def hsga_run_footprint(cfg: hsga_config) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().hsga_run_footprint(ctypes.byref(cfg), ctypes.byref(n)), "hsga_run_footprint")
+    return n.value
+
+
+def hsga_batch_destroy(b):
+    if b:
+        lib().hsga_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper around an hsga_batch (many runs advanced together)."""
+
+    def __init__(self, stream=None):
+        self.handle = hsga_batch_create(stream)
+        self.cfgs = []
+
+    def add(self, generations, **kw) -> int:
+        cfg = make_config(**kw)
+        rid = hsga_batch_add(self.handle, cfg, generations)
+        self.cfgs.append(cfg)
+        return rid
+
+    def run(self, ticks):
+        hsga_batch_run(self.handle, ticks)
+
+    def info(self, run):
+        return hsga_batch_info(self.handle, run)
+
+    def population(self, run):
+        c = self.cfgs[run]
+        agents = c.rows * c.cols * c.agents_per_island
+        t = np.zeros(agents, dtype=np.uint32)
+        s = np.zeros(agents, dtype=np.uint64)
+        hsga_batch_get_population(self.handle, run, t, s)
+        return t, s
+
+    def sample(self, run, k):
+        w = np.zeros((k, 4), dtype=np.uint32)
+        where = np.zeros((k, 2), dtype=np.uint32)
+        hsga_batch_sample(self.handle, run, k, w, where)
+        return w, where
+
+    def remove(self, run):
+        hsga_batch_remove(self.handle, run)
+
+    def stats(self):
+        return hsga_batch_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            hsga_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------- convenience ---

@@ -101,7 +101,7 @@ int validate(const hsga_config *c) {
   if (!(c->p_beneficial >= 0.0 && c->p_beneficial <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (!(c->p_deleterious >= 0.0 && c->p_deleterious <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
-  if (c->kernel > HSGA_KERNEL_RESIDENT || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
+  if (c->kernel > HSGA_KERNEL_RESIDENT_GRID || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
   return HSGA_OK;
 }
 
@@ -243,8 +243,8 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
   }
   g->resident = false;
   if (cfg->kernel != HSGA_KERNEL_STREAMED) {
-    g->resident = resident_plan(g->p, &g->plan);
-    if (!g->resident && cfg->kernel == HSGA_KERNEL_RESIDENT) {
+    g->resident = resident_plan(g->p, &g->plan, cfg->kernel == HSGA_KERNEL_RESIDENT_GRID);
+    if (!g->resident && cfg->kernel >= HSGA_KERNEL_RESIDENT) {
       free_grid(g);
       return HSGA_ERR_UNSUPPORTED;
     }
@@ -314,7 +314,7 @@ int hsga_run_generations(hsga_grid *g, uint64_t n) {
       const uint64_t G = g->G + k;
       const bool do_mig = migrates(g->p, G) && !(g->premigrated && k == 0);
       e = launch_step_streamed(g->p, (uint32_t)G, do_mig, g->trait[g->cur], g->surf[g->cur],
-                               g->trait[1 - g->cur], g->surf[1 - g->cur], g->stream);
+                               g->trait[1 - g->cur], g->surf[1 - g->cur], g->err, g->stream);
       g->cur = 1 - g->cur;
       g->launches++;
     }
@@ -394,7 +394,8 @@ int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
   out->generation = g->G;
   out->replications = g->replications;
   out->kernel_launches = g->launches;
-  out->kernel = g->resident ? HSGA_KERNEL_RESIDENT : HSGA_KERNEL_STREAMED;
+  out->kernel = !g->resident ? HSGA_KERNEL_STREAMED
+                : (g->plan.block_sync ? HSGA_KERNEL_RESIDENT : HSGA_KERNEL_RESIDENT_GRID);
   if (g->resident) {
     out->islands_per_warp = (uint32_t)g->plan.ipw;
     out->warps_per_block = (uint32_t)g->plan.warps_per_block;
@@ -545,4 +546,19 @@ int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint
 namespace hsga {
 int validate_config(const hsga_config *c) { return validate(c); }
 RunParams params_from_config(const hsga_config *c) { return make_params(c); }
+}  // namespace hsga
+
+// Device memory through the registered hooks, for the batch engine
+// (hsga_batch.cu).
+namespace hsga {
+AllocHooks current_allocator() {
+  return AllocHooks{g_allocator.alloc, g_allocator.free_fn, g_allocator.ctx};
+}
+void *device_alloc(const AllocHooks &h, size_t bytes, cudaStream_t s) {
+  return dev_alloc(Allocator{h.alloc, h.free_fn, h.ctx}, bytes, s);
+}
+void device_free(const AllocHooks &h, void *ptr, cudaStream_t s) {
+  dev_free(Allocator{h.alloc, h.free_fn, h.ctx}, ptr, s);
+}
+bool device_pointer(const void *ptr) { return is_device_ptr(ptr); }
 }  // namespace hsga

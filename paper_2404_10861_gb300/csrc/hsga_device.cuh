@@ -223,6 +223,15 @@ __device__ __forceinline__ uint64_t deposit_into(const Deposit &d, uint64_t s, u
   return ((uint64_t)hi << 32) | lo;
 }
 
+// RK: the run's round keys are precomputed in the parameter block (single-run
+// kernels); otherwise they are derived from the key in registers.
+template <bool RK>
+__device__ __forceinline__ Words4 philox_p(const RunParams &p, uint32_t c0, uint32_t c1,
+                                           uint32_t c2, uint32_t c3) {
+  if constexpr (RK) return philox_rk(p, c0, c1, c2, c3);
+  else return philox(p.k0, p.k1, c0, c1, c2, c3);
+}
+
 // Neighbour of island `isl` in direction d (0 N, 1 E, 2 S, 3 W).
 __host__ __device__ __forceinline__ uint32_t neighbour(const RunParams &p, uint32_t isl,
                                                        uint32_t d) {

@@ -20,15 +20,17 @@ struct ResidentPlan {
   int ipw = 0;     // islands per warp
   int blocks = 0;  // cooperative grid
   int warps_per_block = kResidentThreads / 32;
+  bool block_sync = false;  // whole grid in one block: shared-memory records, block barriers
 };
 
+// err: the grid's device error word (bounded waits report timeouts there).
 cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
                                  const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
-                                 uint64_t *sout, cudaStream_t stream);
+                                 uint64_t *sout, int *err, cudaStream_t stream);
 
 // Chooses the resident tile (smallest islands-per-warp whose cooperative
 // grid is co-resident).  Returns false when the grid does not fit on chip.
-bool resident_plan(const RunParams &p, ResidentPlan *out);
+bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only = false);
 
 cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
                                  uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
@@ -42,6 +44,17 @@ size_t sample_scratch_bytes(const RunParams &p, uint32_t k);
 cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint32_t *t,
                           const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
                           uint32_t *scratch, cudaStream_t stream);
+
+// Device memory through the registered allocator hooks (hsga_capi.cu).
+struct AllocHooks {
+  hsga_alloc_fn alloc;
+  hsga_free_fn free_fn;
+  void *ctx;
+};
+AllocHooks current_allocator();
+void *device_alloc(const AllocHooks &h, size_t bytes, cudaStream_t s);
+void device_free(const AllocHooks &h, void *ptr, cudaStream_t s);
+bool device_pointer(const void *ptr);
 
 // Configuration checks and kernel parameters (defined in hsga_capi.cu).
 int validate_config(const hsga_config *c);

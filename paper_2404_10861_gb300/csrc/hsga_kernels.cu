@@ -16,186 +16,8 @@
 namespace hsga {
 
 // ------------------------------------------------------ streamed step ---
-// A warp advances groups of kGroup consecutive islands.  The group's
-// migration draws take one warp-wide Philox evaluation: lane 5p+r (r < 4)
-// evaluates the emigrant block of the neighbour in direction r of island
-// isl0+p and gathers that emigrant's genome from the parent planes when it is
-// aimed at isl0+p; lane 5p+4 evaluates the placement block of isl0+p and
-// turns it into a landing plan: byte d holds the slot where the direction-d
-// immigrant ends up, or 0xFF when it does not arrive or a later direction
-// lands on the same slot (later arrivals overwrite earlier ones).
-constexpr uint32_t kGroup = 6;  // 6 islands x 5 blocks = 30 of 32 lanes
-
-struct GroupMigration {
-  uint32_t plan;  // lane 5p+4: landing plan of island isl0+p
-  uint32_t it;    // lane 5p+r: the direction-r immigrant's genome
-  uint64_t is;
-};
-
-template <bool TRACKED>
-__device__ __forceinline__ void group_migration(const RunParams &p, uint32_t isl0, uint32_t G,
-                                                const uint32_t *__restrict__ tin,
-                                                const uint64_t *__restrict__ sin,
-                                                GroupMigration &gm) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t pi = lane / 5u, role = lane - pi * 5u;
-  const uint32_t isl = isl0 + pi;
-  const bool valid = lane < 5u * kGroup && isl < p.islands;
-  const uint32_t src = valid ? (role == 4 ? isl : neighbour(p, isl, role)) : 0u;
-  const Words4 m =
-      philox_rk(p, role == 4 ? kSlotImmigrant : kSlotEmigrant, src, G, kPurposeMigration);
-  const bool arrive = valid && role < 4 && (m.y >> 30) == ((role + 2u) & 3u);
-  gm.it = 0;
-  gm.is = 0;
-  if (arrive) {
-    const uint32_t a = src * p.n + uindex(m.x, p.n);
-    gm.it = __ldg(tin + a);
-    if constexpr (TRACKED) gm.is = __ldg(sin + a);
-  }
-  const uint32_t arrivals = __ballot_sync(kFull, arrive);
-  const uint32_t bits = (arrivals >> (5u * pi)) & 0xFu;
-  uint32_t b[4] = {uindex(m.x, p.n), uindex(m.y, p.n), uindex(m.z, p.n), uindex(m.w, p.n)};
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    if (!((bits >> d) & 1u)) b[d] = 0xFFu;
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int e = d + 1; e < 4; ++e)
-      if (b[e] == b[d]) b[d] = 0xFFu;
-  gm.plan = (role == 4 && valid) ? (b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24))
-                                 : 0xFFFFFFFFu;
-}
-
-// a2 for island isl0+k: each lane looks its slots up in the landing plan
-// (a zero-byte test on plan ^ slot) and pulls the immigrant from the lane that
-// gathered it.
-template <int AP, bool TRACKED>
-__device__ __forceinline__ void group_land(const GroupMigration &gm, uint32_t k,
-                                           uint32_t (&pt)[AP], uint64_t (&ps)[AP]) {
-  const uint32_t plan = __shfl_sync(kFull, gm.plan, 5u * k + 4u);
-  if (plan == 0xFFFFFFFFu) return;
-  const uint32_t lane = threadIdx.x & 31u;
-#pragma unroll
-  for (int a = 0; a < AP; ++a) {
-    const uint32_t x = plan ^ ((lane + 32u * a) * 0x01010101u);
-    // lowest zero byte of x (at most one byte can match: plan bytes of
-    // surviving directions are distinct)
-    const uint32_t z = (x - 0x01010101u) & ~x & 0x80808080u;
-    const uint32_t d = (uint32_t)(__ffs(z) - 1) >> 3;
-    const uint32_t src = z ? 5u * k + d : lane;
-    const uint32_t vt = __shfl_sync(kFull, gm.it, src);
-    if (z) pt[a] = vt;
-    if constexpr (TRACKED) {
-      const uint64_t vs = shfl64(gm.is, src);
-      if (z) ps[a] = vs;
-    }
-  }
-}
-
-// NN: agents per island known at compile time (32), or 0 for a runtime n.
-template <int AP, bool TRACKED, int NN = 0>
-__device__ __forceinline__ void load_island(const RunParams &p, uint32_t isl,
-                                            const uint32_t *__restrict__ tin,
-                                            const uint64_t *__restrict__ sin, uint32_t (&t)[AP],
-                                            uint64_t (&s)[AP]) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t n = NN ? (uint32_t)NN : p.n;
-  const uint32_t base = isl * n;
-#pragma unroll
-  for (int a = 0; a < AP; ++a) {
-    const uint32_t j = lane + 32u * a;
-    t[a] = 0;
-    s[a] = 0;
-    if (NN == 32 || j < n) {
-      t[a] = __ldcs(tin + base + j);
-      if constexpr (TRACKED) s[a] = __ldcs(sin + base + j);
-    }
-  }
-}
-
-template <int AP, bool TRACKED, int NN = 0>
-__device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
-                                             uint32_t *__restrict__ tout,
-                                             uint64_t *__restrict__ sout,
-                                             const uint32_t (&t)[AP], const uint64_t (&s)[AP]) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t n = NN ? (uint32_t)NN : p.n;
-  const uint32_t base = isl * n;
-#pragma unroll
-  for (int a = 0; a < AP; ++a) {
-    const uint32_t j = lane + 32u * a;
-    if (NN == 32 || j < n) {
-      __stcs(tout + base + j, t[a]);
-      if constexpr (TRACKED) __stcs(sout + base + j, s[a]);
-    }
-  }
-}
-
-// One full group: all six islands' genomes are requested up front (deep
-// memory-level parallelism), then the islands are processed ILV at a time so
-// that each lane runs ILV independent Philox chains (instruction-level
-// parallelism hides the multiply-xor dependency chain of the rounds).
-constexpr int kInterleave = 2;
-
-template <int AP, bool TRACKED, bool T2, int NN, int ILV = kInterleave>
-__device__ __forceinline__ void full_group(const RunParams &p, const Deposit &dep, uint32_t G,
-                                           bool do_mig, uint32_t isl0,
-                                           const uint32_t *__restrict__ tin,
-                                           const uint64_t *__restrict__ sin,
-                                           uint32_t *__restrict__ tout,
-                                           uint64_t *__restrict__ sout) {
-  static_assert(kGroup % ILV == 0, "interleave width must divide the group");
-  uint32_t pt[kGroup][AP];
-  uint64_t ps[kGroup][AP];
-#pragma unroll
-  for (uint32_t k = 0; k < kGroup; ++k)
-    load_island<AP, TRACKED, NN>(p, isl0 + k, tin, sin, pt[k], ps[k]);
-  GroupMigration gm;
-  if (do_mig) group_migration<TRACKED>(p, isl0, G, tin, sin, gm);
-#pragma unroll
-  for (uint32_t k = 0; k < kGroup; k += ILV) {
-    Words4 w[ILV][AP];
-#pragma unroll
-    for (int i = 0; i < ILV; ++i) replication_words<AP>(p, isl0 + k + i, G, w[i]);
-    if (do_mig) {
-#pragma unroll
-      for (int i = 0; i < ILV; ++i) group_land<AP, TRACKED>(gm, k + i, pt[k + i], ps[k + i]);
-    }
-    uint32_t ct[ILV][AP];
-    uint64_t cs[ILV][AP];
-#pragma unroll
-    for (int i = 0; i < ILV; ++i)
-      replicate<AP, TRACKED, T2>(p, dep, isl0 + k + i, G, w[i], pt[k + i], ps[k + i], ct[i],
-                                 cs[i]);
-#pragma unroll
-    for (int i = 0; i < ILV; ++i)
-      store_island<AP, TRACKED, NN>(p, isl0 + k + i, tout, sout, ct[i], cs[i]);
-  }
-}
-
-// The last, partial group: islands one at a time.
-template <int AP, bool TRACKED, bool T2>
-__device__ __noinline__ void partial_group(const RunParams &p, const Deposit &dep, uint32_t G,
-                                           bool do_mig, uint32_t isl0,
-                                           const uint32_t *__restrict__ tin,
-                                           const uint64_t *__restrict__ sin,
-                                           uint32_t *__restrict__ tout,
-                                           uint64_t *__restrict__ sout) {
-  GroupMigration gm;
-  if (do_mig) group_migration<TRACKED>(p, isl0, G, tin, sin, gm);
-  for (uint32_t k = 0; isl0 + k < p.islands; ++k) {
-    uint32_t pt[AP], ct[AP];
-    uint64_t ps[AP], cs[AP];
-    load_island<AP, TRACKED>(p, isl0 + k, tin, sin, pt, ps);
-    Words4 w[AP];
-    replication_words<AP>(p, isl0 + k, G, w);
-    if (do_mig) group_land<AP, TRACKED>(gm, k, pt, ps);
-    replicate<AP, TRACKED, T2>(p, dep, isl0 + k, G, w, pt, ps, ct, cs);
-    store_island<AP, TRACKED>(p, isl0 + k, tout, sout, ct, cs);
-  }
-}
-
+// The group helpers (migration draws, landing plans, island loads/stores)
+// live in hsga_island.cuh.
 template <int AP, bool TRACKED, bool T2, int NN>
 __global__ void __launch_bounds__(kStreamThreads)
     step_streamed_kernel(RunParams p, Deposit dep, uint32_t G, int do_mig,
@@ -241,10 +63,11 @@ static void launch_streamed_t(const RunParams &p, const Deposit &dep, uint32_t G
 
 cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
                                  const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
-                                 uint64_t *sout, cudaStream_t stream) {
+                                 uint64_t *sout, int *err, cudaStream_t stream) {
   const Deposit dep = deposit_for(p, G);
   const bool tracked = p.policy != HSGA_NONE;
   const bool t2 = p.tournament == 2;
+  (void)err;  // the streamed kernel has no waits
 #define HSGA_LAUNCH(AP_, TR_, T2_, NN_) \
   launch_streamed_t<AP_, TR_, T2_, NN_>(p, dep, G, do_mig, tin, sin, tout, sout, stream)
 #define HSGA_LAUNCH_T(AP_, NN_)                         \

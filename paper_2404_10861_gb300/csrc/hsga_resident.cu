@@ -46,22 +46,28 @@ __device__ __forceinline__ uint64_t global_ns() {
 __device__ bool wait_flag(const uint32_t *flag, uint32_t seq, const int *err) {
   if (ld_acquire(flag) >= seq) return true;
   const uint64_t t0 = global_ns();
-  for (;;) {
-    __nanosleep(64);
+  for (uint32_t spin = 1;; ++spin) {
     if (ld_acquire(flag) >= seq) return true;
-    if (*(volatile const int *)err != 0) return false;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if ((spin & 255u) == 0) {
+      if (*(volatile const int *)err != 0) return false;
+      if (global_ns() - t0 > kWaitNs) return false;
+    }
   }
 }
 
-template <int AP, int IPW, bool TRACKED>
-__global__ void __launch_bounds__(kResidentThreads)
+// BLOCKSYNC: the whole grid lives in one thread block (at most 32 warps);
+// records go to shared memory and one __syncthreads per migration replaces
+// the flags (the record buffer of migration m is rewritten at m+2, after the
+// barrier of m+1, which every reader of m has passed).
+template <int AP, int IPW, bool TRACKED, bool BLOCKSYNC>
+__global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
     step_resident_kernel(RunParams p, uint32_t G0, uint32_t ngen, int premigrated,
                          uint32_t *__restrict__ tplane, uint64_t *__restrict__ splane,
                          uint4 *__restrict__ rec, uint32_t *__restrict__ flags,
                          int *__restrict__ err) {
+  __shared__ uint4 srec[BLOCKSYNC ? 2 * 32 * IPW : 1];
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = blockIdx.x * (kResidentThreads / 32) + (threadIdx.x >> 5);
+  const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   uint32_t isl[IPW];
   uint32_t pt[IPW][AP];
   uint64_t ps[IPW][AP];
@@ -126,11 +132,16 @@ __global__ void __launch_bounds__(kResidentThreads)
                 sv = ps[k][1];
               }
             }
-            rec[(size_t)buf * p.islands + isl[k]] =
-                make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
-            st_release(flags + isl[k], seq);
+            const uint4 r = make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
+            if constexpr (BLOCKSYNC) {
+              srec[buf * 32 * IPW + isl[k]] = r;
+            } else {
+              rec[(size_t)buf * p.islands + isl[k]] = r;
+              st_release(flags + isl[k], seq);
+            }
           }
         }
+        if constexpr (BLOCKSYNC) __syncthreads();
       }
 #pragma unroll
       for (int k = 0; k < IPW; ++k) {
@@ -144,18 +155,25 @@ __global__ void __launch_bounds__(kResidentThreads)
           uint64_t is = 0;
           if (lane < 4) {
             const uint32_t nb = neighbour(p, isl[k], lane);
-            ok = wait_flag(flags + nb, seq, err);
+            uint4 r;
+            if constexpr (BLOCKSYNC) {
+              r = srec[buf * 32 * IPW + nb];
+            } else {
+              ok = wait_flag(flags + nb, seq, err);
+              if (ok) r = __ldcg(rec + (size_t)buf * p.islands + nb);
+            }
             if (ok) {
-              const uint4 r = __ldcg(rec + (size_t)buf * p.islands + nb);
               arrive = r.w == ((lane + 2u) & 3u);
               it = r.x;
               is = ((uint64_t)r.z << 32) | r.y;
             }
           }
-          if (__any_sync(kFull, !ok)) {
-            if (lane == 0) atomicCAS(err, 0, kDevErrWaitTimeout);
-            failed = true;
-            break;
+          if constexpr (!BLOCKSYNC) {
+            if (__any_sync(kFull, !ok)) {
+              if (lane == 0) atomicCAS(err, 0, kDevErrWaitTimeout);
+              failed = true;
+              break;
+            }
           }
           const uint32_t arrivals = __ballot_sync(kFull, arrive);
           const uint32_t place[4] = {mig[k].x, mig[k].y, mig[k].z, mig[k].w};
@@ -197,10 +215,15 @@ __global__ void __launch_bounds__(kResidentThreads)
 using ResidentFn = void (*)(RunParams, uint32_t, uint32_t, int, uint32_t *, uint64_t *, uint4 *,
                             uint32_t *, int *);
 
-static ResidentFn pick(int ap, int ipw, bool tracked) {
-#define HSGA_PICK(AP_, IPW_)                                                       \
-  if (ap == AP_ && ipw == IPW_)                                                    \
-    return tracked ? step_resident_kernel<AP_, IPW_, true> : step_resident_kernel<AP_, IPW_, false>;
+static ResidentFn pick(int ap, int ipw, bool tracked, bool block) {
+#define HSGA_PICK(AP_, IPW_)                                                          \
+  if (ap == AP_ && ipw == IPW_) {                                                     \
+    if (block)                                                                        \
+      return tracked ? step_resident_kernel<AP_, IPW_, true, true>                    \
+                     : step_resident_kernel<AP_, IPW_, false, true>;                  \
+    return tracked ? step_resident_kernel<AP_, IPW_, true, false>                     \
+                   : step_resident_kernel<AP_, IPW_, false, false>;                   \
+  }
   HSGA_PICK(1, 1)
   HSGA_PICK(1, 2)
   HSGA_PICK(1, 4)
@@ -210,17 +233,38 @@ static ResidentFn pick(int ap, int ipw, bool tracked) {
   return nullptr;
 }
 
-bool resident_plan(const RunParams &p, ResidentPlan *out) {
+bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
   int dev = 0, sms = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) return false;
   const int ap = p.n <= 32 ? 1 : 2;
-  const int wpb = kResidentThreads / 32;
+  const bool tracked = p.policy != HSGA_NONE;
   const int ipws[3] = {1, 2, 4};
+  // small grids: one thread block, shared-memory records, block barriers
   for (int ipw : ipws) {
-    ResidentFn fn = pick(ap, ipw, p.policy != HSGA_NONE);
+    if (grid_only) break;
+    ResidentFn fn = pick(ap, ipw, tracked, true);
+    if (!fn) continue;
+    const uint64_t warps = ((uint64_t)p.islands + ipw - 1) / ipw;
+    if (warps > 32) continue;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)warps * 32, 0) !=
+        cudaSuccess)
+      return false;
+    if (per_sm >= 1) {
+      out->ap = ap;
+      out->ipw = ipw;
+      out->blocks = 1;
+      out->warps_per_block = (int)warps;
+      out->block_sync = true;
+      return true;
+    }
+  }
+  if (!coop) return false;
+  const int wpb = kResidentThreads / 32;
+  for (int ipw : ipws) {
+    ResidentFn fn = pick(ap, ipw, tracked, false);
     if (!fn) continue;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResidentThreads, 0) !=
@@ -233,6 +277,7 @@ bool resident_plan(const RunParams &p, ResidentPlan *out) {
       out->ipw = ipw;
       out->blocks = (int)blocks;
       out->warps_per_block = wpb;
+      out->block_sync = false;
       return true;
     }
   }
@@ -242,10 +287,14 @@ bool resident_plan(const RunParams &p, ResidentPlan *out) {
 cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
                                  uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
                                  uint4 *rec, uint32_t *flags, int *err, cudaStream_t stream) {
-  ResidentFn fn = pick(plan.ap, plan.ipw, p.policy != HSGA_NONE);
+  ResidentFn fn = pick(plan.ap, plan.ipw, p.policy != HSGA_NONE, plan.block_sync);
   if (!fn) return cudaErrorInvalidValue;
   RunParams pp = p;
   int prem = premigrated ? 1 : 0;
+  if (plan.block_sync) {
+    fn<<<1, plan.warps_per_block * 32, 0, stream>>>(pp, G0, ngen, prem, t, s, rec, flags, err);
+    return cudaGetLastError();
+  }
   void *args[] = {&pp, &G0, &ngen, &prem, &t, &s, &rec, &flags, &err};
   return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.blocks),
                                      dim3(kResidentThreads), args, 0, stream);

@@ -20,7 +20,7 @@ from paper_2404_10861_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = {"streamed": 1, "resident": 2}
+KERNELS = {"streamed": 1, "resident": 2, "resident_grid": 3}
 
 
 @pytest.fixture(scope="module")
@@ -67,13 +67,13 @@ def assert_same(a, b, what):
     assert len(bad_s) == 0, f"{what}: {len(bad_s)} surfaces differ, first at agent {bad_s[:5]}"
 
 
-@pytest.mark.parametrize("kernel", ["streamed", "resident"])
+@pytest.mark.parametrize("kernel", ["streamed", "resident", "resident_grid"])
 def test_tiny_workload_full_run(hb, orc, kernel):
     kw = dict(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, p_ben=0.0, seed=1)
     want = orc.run(oracle_cfg(orc, kw), generations=2000)[:2]
     t, s, st = gpu_run(hb, kw, kernel, chunks=(1, 99, 1900))
     assert st["generation"] == 2000
-    assert st["kernel"] == KERNELS[kernel]
+    assert st["kernel"] == KERNELS[kernel]            # tiny grid: one block when resident
     assert_same((t, s), want, f"tiny/{kernel}")
     assert not t.any()                      # neutral: traits stay 0
     assert s.any()
@@ -106,7 +106,7 @@ EDGE = [
 ]
 
 
-@pytest.mark.parametrize("kernel", ["streamed", "resident"])
+@pytest.mark.parametrize("kernel", ["streamed", "resident", "resident_grid"])
 @pytest.mark.parametrize("case", range(len(EDGE)))
 def test_edge_shapes_from_random_states(hb, orc, kernel, case):
     kw = dict(EDGE[case], seed=100 + case)
@@ -123,7 +123,7 @@ def test_edge_shapes_from_random_states(hb, orc, kernel, case):
         assert_same((t, s), want, f"edge{case}/{kernel}/G0={G0}")
 
 
-@pytest.mark.parametrize("kernel", ["streamed", "resident"])
+@pytest.mark.parametrize("kernel", ["streamed", "resident", "resident_grid"])
 def test_explicit_migrate_then_run(hb, orc, kernel):
     kw = dict(rows=5, cols=8, n=20, tournament=2, policy="tilted", bits=2, p_ben=0.02, seed=9)
     c = oracle_cfg(orc, kw)
@@ -256,7 +256,12 @@ def test_torch_allocator_and_stream(hb, orc):
 def test_kernel_choice(hb):
     g = hb.Grid(rows=64, cols=64, n=32)
     try:
-        assert g.stats()["kernel"] == 2                   # mid grid fits on chip
+        assert g.stats()["kernel"] == 3                   # mid grid: cooperative resident grid
+    finally:
+        g.close()
+    g = hb.Grid(rows=4, cols=4, n=32)
+    try:
+        assert g.stats()["kernel"] == 2                   # tiny grid: one resident block
     finally:
         g.close()
 
