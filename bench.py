@@ -454,6 +454,37 @@ def run_batched(args):
         "speedup": t_plain / t_batch, "dtype": "u32", "data": "synthetic"}), flush=True)
 
 
+def run_served(args):
+    """Served experiments: a Poisson stream of runs served by continuous
+    batching against the same stream served one run at a time."""
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb, serve
+    _build.build()
+    torch.cuda.set_device(0)
+    hb.use_torch_allocator()
+    rate = 20.0 * args.gen_scale      # keeps the offered load of the full-size stream
+    reqs = serve.poisson_requests(args.requests, rate, seed=5, gen_scale=args.gen_scale)
+    offered = sum(r.agents * r.generations for r in reqs) / reqs[-1].arrival
+    stream = torch.cuda.Stream()
+    cap = args.memory_cap_mb * 2**20
+    res_b, st_b = serve.serve(reqs, memory_cap=cap, stream=stream.cuda_stream)
+    res_a, st_a = serve.serve_alone(reqs, stream=stream.cuda_stream)
+    same = sum(int(np.array_equal(a.words, b.words) and np.array_equal(a.where, b.where))
+               for a, b in zip(sorted(res_a, key=lambda r: r.rid),
+                               sorted(res_b, key=lambda r: r.rid)))
+    print(json.dumps({
+        "metric": "runs/hour and p50/p99 completion latency, continuous batching vs alone",
+        "workload": f"{args.requests} requests, Poisson {rate:g}/s, agents log-uniform "
+                    f"[1024, 4194304] (32 per island, near-square torus), generations "
+                    f"log-uniform [1000, 100000] / {args.gen_scale}, random policy and "
+                    f"adaptive flag, seed 5, 10,000-genome samples",
+        "offered_agent_replications_per_s": offered,
+        "memory_cap_bytes": cap,
+        "served": serve.summarize(res_b, st_b), "alone": serve.summarize(res_a, st_a),
+        "results_identical_alone_and_in_the_mix": f"{same}/{len(reqs)}",
+        "dtype": "u32", "data": "synthetic"}), flush=True)
+
+
 def run_profile(gens: int):
     """Workload only, for profilers: founders, `gens` generations, one sample."""
     import torch
@@ -478,13 +509,20 @@ def main():
     ap.add_argument("--profile-gens", type=int, default=0,
                     help="profiling mode: only run this many generations of the workload "
                          "(no timing); used for ncu captures")
-    ap.add_argument("--workload", default="wafer", choices=["wafer", "tiny", "mid", "batched"],
-                    help="wafer: the benchmark line; tiny / mid / batched: informational lines")
+    ap.add_argument("--workload", default="wafer",
+                    choices=["wafer", "tiny", "mid", "batched", "served"],
+                    help="wafer: the benchmark line; the others: informational lines")
+    ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
+    ap.add_argument("--memory-cap-mb", type=int, default=2048,
+                    help="served workload: device memory cap for admission")
     ap.add_argument("--gen-scale", type=int, default=100,
                     help="batched workload: divide the generation budgets by this")
     args = ap.parse_args()
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
     if args.workload != "wafer":
         if args.warmup < 3:

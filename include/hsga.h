@@ -273,6 +273,9 @@ int hsga_batch_get_stats(const hsga_batch *b, hsga_batch_stats *out);
  * memory footprint).  Host function. */
 int hsga_run_footprint(const hsga_config *cfg, uint64_t *bytes);
 
+/* Waits for the batch's stream (all ticks issued so far). */
+int hsga_batch_synchronize(hsga_batch *b);
+
 void hsga_batch_destroy(hsga_batch *b);
 
 /* Allocation-free variant of hsga_run_generations for callers that must not

@@ -106,6 +106,7 @@ _SIGS = {
     "hsga_batch_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_batch_stats)], ctypes.c_int),
     "hsga_run_footprint": ([ctypes.POINTER(hsga_config), ctypes.POINTER(ctypes.c_uint64)],
                            ctypes.c_int),
+    "hsga_batch_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_batch_destroy": ([ctypes.c_void_p], None),
     "hsga_run_generations_noalloc": ([ctypes.POINTER(hsga_config), ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
@@ -367,6 +368,9 @@ class Batch:
 
     def stats(self):
         return hsga_batch_get_stats(self.handle)
+
+    def sync(self):
+        _check(lib().hsga_batch_synchronize(self.handle), "hsga_batch_synchronize")
 
     def close(self):
         if self.handle:

@@ -567,6 +567,11 @@ int hsga_run_footprint(const hsga_config *cfg, uint64_t *bytes) {
   return HSGA_OK;
 }
 
+int hsga_batch_synchronize(hsga_batch *b) {
+  if (!b) return HSGA_ERR_INVALID_ARG;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? HSGA_OK : HSGA_ERR_CUDA;
+}
+
 void hsga_batch_destroy(hsga_batch *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);

@@ -1,0 +1,171 @@
+"""Continuous-batching server for evolution experiments.
+
+Requests (one island-model GA run each: grid, agents per island, policy,
+adaptation, generation budget) arrive over time.  The server keeps admitted
+runs resident on the device inside one batch (``hsga_batch_*``, which
+advances every active run by one generation per tick in one launch),
+admits waiting requests first-come-first-served whenever their device-memory
+footprint fits under a cap, advances the batch in slices of generations,
+and when a run finishes returns its sampled surfaces (step a7) and frees its
+memory.  Requests that arrive while others are on the GPU join between
+slices, so their work overlaps.  ``serve_alone`` is the reference policy:
+the same stream served one request at a time, each on its own grid.
+
+Every run's result is the same whether it ran alone or in the mix (the batch
+engine is bit-identical to a lone grid); tests check that on sampled output.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding as hb
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float            # seconds after the stream starts
+    config: dict              # keyword arguments of binding.make_config
+    generations: int
+    sample_k: int
+
+    @property
+    def agents(self) -> int:
+        return self.config["rows"] * self.config["cols"] * self.config["n"]
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    replications: int
+    words: np.ndarray = field(repr=False)
+    where: np.ndarray = field(repr=False)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def splitmix64(x: int) -> int:
+    x = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return x ^ (x >> 31)
+
+
+def poisson_requests(count: int, rate: float, seed: int = 5, gen_scale: int = 1,
+                     agents_range=(1024, 4_194_304), gens_range=(1000, 100_000),
+                     sample_k: int = 10_000, n: int = 32):
+    """The served-experiments stream: Poisson arrivals at `rate` per second;
+    agents log-uniform over agents_range mapped to n agents per island on a
+    near-square torus (rows = 2^floor(log2 sqrt(islands)), cols =
+    ceil(islands / rows)); generations log-uniform over gens_range divided by
+    gen_scale; random policy (steady / tilted / stretched) and adaptive flag."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        agents = math.exp(rng.uniform(math.log(agents_range[0]), math.log(agents_range[1])))
+        islands = max(1, math.ceil(agents / n))
+        rows = 2 ** int(math.floor(math.log2(math.sqrt(islands))))
+        cols = math.ceil(islands / rows)
+        gens = int(math.exp(rng.uniform(math.log(gens_range[0]), math.log(gens_range[1]))))
+        gens = max(1, gens // gen_scale)
+        policy = str(rng.choice(["steady", "tilted", "stretched"]))
+        p_ben = 1e-3 if rng.random() < 0.5 else 0.0
+        cfg = dict(rows=rows, cols=cols, n=n, tournament=2, policy=policy, bits=1, W=2,
+                   interval=1, p_ben=p_ben, p_del=0.0, seed=splitmix64((seed << 32) | i))
+        out.append(Request(i, t, cfg, gens, min(sample_k, rows * cols)))
+    return out
+
+
+def _wait_until(t0: float, rel: float):
+    while time.perf_counter() - t0 < rel:
+        time.sleep(min(0.0005, max(0.0, rel - (time.perf_counter() - t0))))
+
+
+def serve(requests, memory_cap: int, slice_ticks: int = 256, stream=None):
+    """Continuous batching.  Returns (results, stats)."""
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    waiting: deque = deque()
+    running = {}                       # run id -> (request, admitted time, footprint)
+    results = []
+    in_use = 0
+    peak_runs = 0
+    blocked = 0                        # admissions deferred by the memory cap
+    with hb.Batch(stream=stream) as batch:
+        t0 = time.perf_counter()
+        while pending or waiting or running:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            while waiting:
+                req = waiting[0]
+                fp = hb.hsga_run_footprint(hb.make_config(**req.config))
+                if fp > memory_cap:
+                    raise ValueError(f"request {req.rid} needs {fp} bytes, over the cap")
+                if in_use + fp > memory_cap:
+                    blocked += 1
+                    break
+                waiting.popleft()
+                rid = batch.add(req.generations, **req.config)
+                running[rid] = (req, time.perf_counter() - t0, fp)
+                in_use += fp
+            peak_runs = max(peak_runs, len(running))
+            if not running:
+                if pending:
+                    _wait_until(t0, pending[0].arrival)
+                continue
+            remaining = min(req.generations - batch.info(rid)["generation"]
+                            for rid, (req, _, _) in running.items())
+            batch.run(max(1, min(slice_ticks, remaining)))
+            batch.sync()          # one slice in flight: arrivals join at the next slice
+            for rid in [r for r in running if batch.info(r)["done"]]:
+                req, admitted, fp = running.pop(rid)
+                words, where = batch.sample(rid, req.sample_k)       # synchronous
+                results.append(Result(req.rid, req.arrival, admitted,
+                                      time.perf_counter() - t0,
+                                      req.agents * req.generations, words, where))
+                batch.remove(rid)
+                in_use -= fp
+        elapsed = time.perf_counter() - t0
+        st = batch.stats()
+    return results, {"elapsed_s": elapsed, "peak_concurrent_runs": peak_runs,
+                     "admissions_deferred": blocked, "kernel_launches": st["kernel_launches"],
+                     "ticks": st["tick"]}
+
+
+def serve_alone(requests, stream=None):
+    """Reference policy: first come, first served, one run at a time."""
+    results = []
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: r.arrival):
+        _wait_until(t0, req.arrival)
+        start = time.perf_counter() - t0
+        with hb.Grid(stream=stream, **req.config) as g:
+            g.run(req.generations)
+            words, where = g.sample(req.sample_k)
+        results.append(Result(req.rid, req.arrival, start, time.perf_counter() - t0,
+                              req.agents * req.generations, words, where))
+    return results, {"elapsed_s": time.perf_counter() - t0}
+
+
+def summarize(results, stats) -> dict:
+    lat = np.array([r.latency for r in results])
+    reps = sum(r.replications for r in results)
+    el = stats["elapsed_s"]
+    out = {"completed": len(results), "runs_per_hour": len(results) * 3600.0 / el,
+           "agent_replications_per_s": reps / el,
+           "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+           "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None}
+    out.update(stats)
+    return out
