@@ -24,9 +24,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hsga_oracle.c")
 _LIB = os.path.join(_HERE, "libhsga_oracle.so")
 
-STEADY, TILTED, STRETCHED, TRIVIAL, NONE = 0, 1, 2, 3, 4
+STEADY, TILTED, STRETCHED, TRIVIAL, NONE, HYBRID = 0, 1, 2, 3, 4, 5
 POLICY_NAMES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
-                "trivial": TRIVIAL, "none": NONE}
+                "trivial": TRIVIAL, "none": NONE, "hybrid": HYBRID}
 REC_WORDS = 6
 
 
@@ -46,7 +46,8 @@ class _Cfg(ctypes.Structure):
                 ("policy", ctypes.c_uint32), ("bits", ctypes.c_uint32),
                 ("W", ctypes.c_uint32), ("interval", ctypes.c_uint32),
                 ("p_ben", ctypes.c_double), ("p_del", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("coarsen", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 @dataclass
@@ -56,7 +57,9 @@ class Config:
     rows x cols toroidal island grid, ``n`` agents per island, tournament size,
     surface policy, differentia bit width (S = 64 / bits surface sites),
     sites per level W (tilted / stretched), migration interval (0 = none),
-    beneficial / deleterious mutation probabilities and the Philox seed.
+    beneficial / deleterious mutation probabilities, the Philox seed, and
+    the annotation interval (temporal coarsening: deposit every coarsen-th
+    generation).
     """
     rows: int = 4
     cols: int = 4
@@ -69,6 +72,7 @@ class Config:
     p_ben: float = 0.0
     p_del: float = 0.0
     seed: int = 1
+    coarsen: int = 1
 
     @property
     def islands(self) -> int:
@@ -85,7 +89,7 @@ class Config:
     def _c(self) -> _Cfg:
         return _Cfg(self.rows, self.cols, self.n, self.tournament, self.policy,
                     self.bits, self.W, self.interval, self.p_ben, self.p_del,
-                    self.seed)
+                    self.seed, self.coarsen, 0)
 
 
 _lib = None

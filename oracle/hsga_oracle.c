@@ -39,7 +39,10 @@
  *   a6 deposit   : site = site_fn(policy, S, W, T); unless the policy discards
  *                  this deposition, surface bits [site*b, site*b + b) take the
  *                  low b bits of w3.  T, the deposition counter, is then one
- *                  larger; in synchronous mode T equals the generation G.
+ *                  larger; in synchronous mode T equals the generation G.  With
+ *                  temporal coarsening k, only generations divisible by k
+ *                  deposit, as deposition G / k.  The hybrid policy writes a
+ *                  second differentia (bits 16.. of w3) into its tilted half.
  *   a7 sample    : one genome per island at slot floor(w0*n/2^32) of
  *                  Philox(key; 0xFFFFFFFD, island, G, 0), then k islands
  *                  without replacement by a partial Fisher-Yates shuffle whose
@@ -113,7 +116,7 @@ static void orc_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
 /* Surface site selection (readings; see header). */
 
 enum { ORC_STEADY = 0, ORC_TILTED = 1, ORC_STRETCHED = 2, ORC_TRIVIAL = 3,
-       ORC_NONE = 4 };
+       ORC_NONE = 4, ORC_HYBRID = 5 };
 
 static unsigned orc_bitlen(uint64_t x) {
   unsigned n = 0;
@@ -128,8 +131,14 @@ static unsigned orc_ctz(uint64_t x) { /* x > 0 */
 }
 
 /* Returns the site in [0, S) written by deposition number T, or S when the
- * policy discards that deposition.  S is a power of two; W divides S. */
+ * policy discards that deposition.  S is a power of two; W divides S.  For
+ * the hybrid policy this is the site of its steady half (sites [0, S/2));
+ * see orc_hybrid_second_site for its tilted half. */
 uint32_t orc_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T) {
+  if (policy == ORC_HYBRID) {
+    uint32_t a = orc_site(ORC_STEADY, S / 2, W, T);
+    return a < S / 2 ? a : S;
+  }
   if (policy == ORC_TRIVIAL) return (uint32_t)(T % S);
   if (policy == ORC_STEADY) {
     /* Epoch e: zero while the first S depositions fill the buffer, then
@@ -165,6 +174,16 @@ uint32_t orc_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T) {
   return S; /* ORC_NONE: no surface */
 }
 
+/* Hybrid policy (the paper's suggestion to give half of the annotation space
+ * to each strategy): every deposition writes two differentiae, one into the
+ * steady half (sites [0, S/2)) and one into the tilted half (sites
+ * [S/2, S)), each half curated by its policy over S/2 sites.  Site of the
+ * tilted half, or S when discarded. */
+uint32_t orc_hybrid_second_site(uint32_t S, uint32_t W, uint64_t T) {
+  uint32_t b = orc_site(ORC_TILTED, S / 2, W, T);
+  return b < S / 2 ? S / 2 + b : S;
+}
+
 /* Definition of the timestamp lookup: for every site, the largest deposition
  * time t < T that wrote it, or -1 if none did.  Brute-force replay. */
 void orc_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
@@ -173,6 +192,10 @@ void orc_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
   for (uint64_t t = 0; t < T; ++t) {
     uint32_t site = orc_site(policy, S, W, t);
     if (site < S) times_out[site] = (int64_t)t;
+    if (policy == ORC_HYBRID) {
+      uint32_t second = orc_hybrid_second_site(S, W, t);
+      if (second < S) times_out[second] = (int64_t)t;
+    }
   }
 }
 
@@ -184,6 +207,8 @@ typedef struct orc_cfg {
   uint32_t policy, bits, W, interval;
   double p_ben, p_del;
   uint64_t seed;
+  uint32_t coarsen; /* annotate every coarsen-th generation (0 or 1: every one) */
+  uint32_t pad;
 } orc_cfg;
 
 enum { ORC_N = 0, ORC_E = 1, ORC_S = 2, ORC_W = 3 };
@@ -270,7 +295,15 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
   uint64_t thr_b = orc_threshold(cfg->p_ben);
   uint64_t thr_d = orc_threshold(cfg->p_del);
   uint32_t S = 64 / cfg->bits;
-  uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
+  /* Temporal coarsening (the paper's suggestion to update annotations only
+   * every k-th generation): generation T deposits only when k divides it,
+   * as deposition number T / k. */
+  uint32_t k = cfg->coarsen > 1 ? cfg->coarsen : 1;
+  int annotate = (T % k) == 0;
+  uint64_t Td = T / k;
+  uint32_t site = annotate ? orc_site(cfg->policy, S, cfg->W, Td) : S;
+  uint32_t site2 = (annotate && cfg->policy == ORC_HYBRID)
+                       ? orc_hybrid_second_site(S, cfg->W, Td) : S;
   uint64_t vmask = (cfg->bits == 64) ? ~0ull : ((1ull << cfg->bits) - 1);
   for (uint32_t l = 0; l < n_local; ++l) {
     if (active && !active[l]) continue;
@@ -301,11 +334,17 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
       } else if ((uint64_t)w[2] < thr_b + thr_d) {
         if (trait != 0) trait -= 1;
       }
-      /* a6: deposit the new differentia. */
+      /* a6: deposit the new differentia (the hybrid policy's second one is
+       * taken from bits 16.. of the same word). */
       if (cfg->policy != ORC_NONE && site < S) {
         uint32_t shift = site * cfg->bits;
         surface &= ~(vmask << shift);
         surface |= ((uint64_t)w[3] & vmask) << shift;
+      }
+      if (cfg->policy != ORC_NONE && site2 < S) {
+        uint32_t shift = site2 * cfg->bits;
+        surface &= ~(vmask << shift);
+        surface |= ((uint64_t)(w[3] >> 16) & vmask) << shift;
       }
       size_t ca = (size_t)l * n + j;
       trait_out[ca] = trait;

@@ -69,10 +69,15 @@ def differentiae(surf: np.ndarray, bits: int) -> np.ndarray:
     return ((surf[:, None] >> shifts[None, :]) & mask).astype(np.int64)
 
 
-def retained_order(policy: int, S: int, W: int, T: int):
-    """Sites holding a differentia after T depositions, in ascending
-    deposition time, and those times."""
-    times = lookup(policy, S, W, T)
+def retained_order(policy: int, S: int, W: int, T: int, coarsen: int = 1):
+    """Sites holding a differentia after T generations, in ascending
+    deposition time, and those times in generations.  With temporal
+    coarsening k the generations 0, k, 2k, ... deposit, so after T
+    generations ceil(T / k) depositions exist and deposition t is generation
+    t k."""
+    k = max(1, coarsen)
+    times = lookup(policy, S, W, -(-T // k)) * k
+    times[times < 0] = -1
     sites = np.nonzero(times >= 0)[0]
     order = sites[np.argsort(times[sites], kind="stable")]
     return order, times[order]
@@ -113,10 +118,12 @@ class Tree:
         return ch
 
 
-def reconstruct(surf: np.ndarray, policy: int, bits: int, W: int, T: int) -> Tree:
-    """Trie reconstruction from sampled surfaces sharing deposition count T."""
+def reconstruct(surf: np.ndarray, policy: int, bits: int, W: int, T: int,
+                coarsen: int = 1) -> Tree:
+    """Trie reconstruction from sampled surfaces that all elapsed T
+    generations."""
     S = 64 // bits
-    order, times = retained_order(policy, S, W, T)
+    order, times = retained_order(policy, S, W, T, coarsen)
     D = differentiae(surf, bits)[:, order]
     parent, time = [-1], [-1]
     kids = [dict()]  # per node: value -> child node

@@ -1,0 +1,75 @@
+"""Pins for the surface variants the paper suggests ("Distributed
+Phylogenetic Tracking": a hybrid giving half the annotation space to each of
+steady and tilted; "Surface Algorithm Benchmark": coarsening the temporal
+resolution by annotating only every k-th generation)."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import phylo
+from paper_2404_10861_gb300 import inputs
+
+HYBRID = 5
+
+
+@pytest.mark.parametrize("S,W", [(64, 2), (32, 2), (16, 2), (64, 4)])
+def test_hybrid_halves_are_steady_and_tilted(orc, S, W):
+    for T in list(range(0, 300)) + [1000, 4097, 65536]:
+        got = orc.lookup(HYBRID, S, W, T)
+        assert list(got[:S // 2]) == list(orc.lookup(orc.STEADY, S // 2, W, T))
+        assert list(got[S // 2:]) == list(orc.lookup(orc.TILTED, S // 2, W, T))
+
+
+def test_hybrid_deposits_two_independent_differentiae(orc):
+    c = orc.Config(rows=16, cols=16, n=32, policy=HYBRID, bits=2, interval=0, seed=3)
+    trait, surf = inputs.small_trait_population(c.agents, seed=2)
+    S, T = 32, 77
+    _, child, par = orc.run(c, trait, surf, G0=T, generations=1, track_parents=True)
+    parent = surf[par[0].astype(np.int64)]
+    sa = orc.site(orc.STEADY, S // 2, 2, T)
+    sb = S // 2 + orc.site(orc.TILTED, S // 2, 2, T)
+    mask = np.uint64(0)
+    for s_ in (sa, sb):
+        if s_ < S:
+            mask |= np.uint64(3 << (2 * s_))
+    assert np.all(((child ^ parent) & ~mask) == 0)
+    va = ((child >> np.uint64(2 * sa)) & np.uint64(3)).astype(np.int64)
+    vb = ((child >> np.uint64(2 * sb)) & np.uint64(3)).astype(np.int64)
+    table = np.zeros((4, 4))
+    np.add.at(table, (va, vb), 1)
+    assert stats.chi2_contingency(table).pvalue > 1e-4           # independent
+    assert stats.chisquare(table.sum(axis=1)).pvalue > 1e-4      # uniform
+
+
+@pytest.mark.parametrize("k", [2, 3, 8])
+def test_coarsening_deposits_every_kth_generation(orc, k):
+    c = orc.Config(rows=8, cols=8, n=16, policy=orc.TILTED, bits=1, interval=0, seed=4,
+                   coarsen=k)
+    trait, surf = inputs.random_population(c.agents, seed=k, trait_max=3)
+    for G in range(0, 3 * k + 1):
+        _, child, par = orc.run(c, trait, surf, G0=G, generations=1, track_parents=True)
+        parent = surf[par[0].astype(np.int64)]
+        changed = child ^ parent
+        if G % k:
+            assert not changed.any()
+        else:
+            s_ = orc.site(orc.TILTED, 64, 2, G // k)
+            assert np.all((changed & ~np.uint64(1 << s_)) == 0)
+            assert changed.any()
+
+
+def test_coarsened_ancestry_bounds(orc):
+    """With coarsening the retained times are generations t k; mismatches
+    still only occur at or after the true split."""
+    k = 4
+    c = orc.Config(rows=4, cols=4, n=16, policy=orc.TILTED, bits=1, seed=8, coarsen=k)
+    G = 600
+    _, surf, par = orc.run(c, generations=G, track_parents=True)
+    order, times = phylo.retained_order(c.policy, 64, 2, G, coarsen=k)
+    assert np.all(times % k == 0)
+    D = phylo.differentiae(surf, 1)[:, order]
+    rng = np.random.default_rng(0)
+    for _ in range(400):
+        x, y = rng.choice(c.agents, size=2, replace=False)
+        d_true = phylo.true_mrca_generation(par, int(x), int(y))
+        assert np.array_equal(D[x, times < d_true], D[y, times < d_true])
