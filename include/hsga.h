@@ -71,13 +71,18 @@ typedef enum hsga_status {
  *             the last W depositions of every level;
  *   stretched same levels, keeps the first W depositions of every level;
  *   trivial   site = T mod S (the paper's benchmark control);
- *   none      no surface (the paper's untracked 32-bit genome). */
+ *   none      no surface (the paper's untracked 32-bit genome);
+ *   hybrid    half of the sites steady and half tilted, each over S/2 sites
+ *             (the paper's suggestion of splitting annotation space between
+ *             the two): every deposition writes two differentiae, the second
+ *             from bits 16.. of the random word. */
 typedef enum hsga_policy {
   HSGA_STEADY = 0,
   HSGA_TILTED = 1,
   HSGA_STRETCHED = 2,
   HSGA_TRIVIAL = 3,
-  HSGA_NONE = 4
+  HSGA_NONE = 4,
+  HSGA_HYBRID = 5
 } hsga_policy;
 
 /* Which kernel advances generations. */
@@ -103,7 +108,9 @@ typedef struct hsga_config {
   double p_deleterious;
   uint64_t seed;                /* Philox key (low word, high word) */
   uint32_t kernel;              /* hsga_kernel */
-  uint32_t reserved;            /* must be 0 */
+  uint32_t deposit_interval;    /* temporal coarsening k: only generations G with
+                                   k | G deposit, as deposition G / k (0 or 1:
+                                   every generation) */
 } hsga_config;
 
 typedef struct hsga_stats {
@@ -195,7 +202,10 @@ uint32_t hsga_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T);
 /* Timestamp lookup: deposition time held by every site after T depositions,
  * from (site, T) alone (section "Distributed Phylogenetic Tracking": no
  * stored timestamps).  times_out: S int64 (host), -1 for a site never
- * written.  Closed form, O(S).  Host function. */
+ * written.  Closed form, O(S).  Host function.  With temporal coarsening k,
+ * G generations make T = ceil(G / k) depositions and deposition t happened
+ * at generation t k.  For the hybrid policy hsga_site returns the site of
+ * its steady half; hsga_lookup covers both halves. */
 int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
                 int64_t *times_out);
 

@@ -17,9 +17,9 @@ import numpy as np
 
 from . import _build
 
-STEADY, TILTED, STRETCHED, TRIVIAL, NONE = 0, 1, 2, 3, 4
+STEADY, TILTED, STRETCHED, TRIVIAL, NONE, HYBRID = 0, 1, 2, 3, 4, 5
 POLICIES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
-            "trivial": TRIVIAL, "none": NONE}
+            "trivial": TRIVIAL, "none": NONE, "hybrid": HYBRID}
 KERNEL_AUTO, KERNEL_STREAMED, KERNEL_RESIDENT, KERNEL_RESIDENT_GRID = 0, 1, 2, 3
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed",
@@ -40,7 +40,7 @@ class hsga_config(ctypes.Structure):
                 ("sites_per_level", ctypes.c_uint32), ("migration_interval", ctypes.c_uint32),
                 ("p_beneficial", ctypes.c_double), ("p_deleterious", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("deposit_interval", ctypes.c_uint32)]
 
 
 class hsga_stats(ctypes.Structure):
@@ -186,10 +186,11 @@ def use_default_allocator():
 
 # ------------------------------------------------------------ functions ---
 def make_config(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2,
-                interval=1, p_ben=0.0, p_del=0.0, seed=1, kernel=KERNEL_AUTO) -> hsga_config:
+                interval=1, p_ben=0.0, p_del=0.0, seed=1, kernel=KERNEL_AUTO,
+                coarsen=1) -> hsga_config:
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return hsga_config(rows, cols, n, tournament, pol, bits, W, interval, p_ben, p_del,
-                       seed, kernel, 0)
+                       seed, kernel, coarsen)
 
 
 def hsga_init_grid(cfg: hsga_config, cuda_stream=None) -> ctypes.c_void_p:

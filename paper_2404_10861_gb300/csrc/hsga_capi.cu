@@ -91,17 +91,20 @@ int validate(const hsga_config *c) {
   if ((uint64_t)c->rows * c->cols * c->agents_per_island >= 0xFFFFFFFFull)
     return HSGA_ERR_INVALID_ARG;
   if (c->tournament_size == 0 || c->tournament_size > 64) return HSGA_ERR_INVALID_ARG;
-  if (c->surface_policy > HSGA_NONE) return HSGA_ERR_INVALID_ARG;
+  if (c->surface_policy > HSGA_HYBRID) return HSGA_ERR_INVALID_ARG;
   const uint32_t b = c->differentia_bits;
   if (!(b == 1 || b == 2 || b == 4 || b == 8)) return HSGA_ERR_INVALID_ARG;
   const uint32_t S = 64 / b, W = c->sites_per_level;
   if (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED) {
     if (!(W == 1 || W == 2 || W == 4) || S / W < 2) return HSGA_ERR_INVALID_ARG;
   }
+  if (c->surface_policy == HSGA_HYBRID) {  // two halves of S/2 sites each
+    if (!(W == 1 || W == 2 || W == 4) || (S / 2) / W < 2) return HSGA_ERR_INVALID_ARG;
+  }
   if (!(c->p_beneficial >= 0.0 && c->p_beneficial <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (!(c->p_deleterious >= 0.0 && c->p_deleterious <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
-  if (c->kernel > HSGA_KERNEL_RESIDENT_GRID || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
+  if (c->kernel > HSGA_KERNEL_RESIDENT_GRID) return HSGA_ERR_INVALID_ARG;
   return HSGA_OK;
 }
 
@@ -119,9 +122,11 @@ RunParams make_params(const hsga_config *c) {
   p.policy = c->surface_policy;
   p.bits = c->differentia_bits;
   p.S = 64 / p.bits;
-  p.W = (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED)
+  p.W = (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED ||
+         c->surface_policy == HSGA_HYBRID)
             ? c->sites_per_level
             : 2;
+  p.coarsen = c->deposit_interval > 1 ? c->deposit_interval : 1;
   p.interval = c->migration_interval;
   const uint64_t thr_ben = threshold(c->p_beneficial);
   const uint64_t thr_bd = thr_ben + threshold(c->p_deleterious);  // <= 2^32 (validated)
@@ -458,16 +463,22 @@ int hsga_load(hsga_grid *g, const void *buf, size_t len) {
 void hsga_destroy(hsga_grid *g) { free_grid(g); }
 
 uint32_t hsga_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T) {
-  if (policy > HSGA_NONE || !power_of_two(S) || S < 2) return S;
+  if (policy > HSGA_HYBRID || !power_of_two(S) || S < 2) return S;
   if ((policy == HSGA_TILTED || policy == HSGA_STRETCHED) && (!power_of_two(W) || S / W < 2))
     return S;
+  if (policy == HSGA_HYBRID && S < 4) return S;
   return site_of(policy, S, W, T);
 }
 
 // Closed-form timestamp lookup (see hsga.h for the site functions it inverts).
 int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *out) {
-  if (!out || !power_of_two(S) || S < 2 || S > 64 || policy > HSGA_NONE)
+  if (!out || !power_of_two(S) || S < 2 || S > 64 || policy > HSGA_HYBRID)
     return HSGA_ERR_INVALID_ARG;
+  if (policy == HSGA_HYBRID) {  // steady half, then tilted half
+    if (S < 4) return HSGA_ERR_INVALID_ARG;
+    const int r = hsga_lookup(HSGA_STEADY, S / 2, W, N, out);
+    return r != HSGA_OK ? r : hsga_lookup(HSGA_TILTED, S / 2, W, N, out + S / 2);
+  }
   for (uint32_t i = 0; i < S; ++i) out[i] = -1;
   if (N == 0 || policy == HSGA_NONE) return HSGA_OK;
   if (policy == HSGA_TRIVIAL) {
@@ -532,7 +543,8 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *ou
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
                       uint32_t *out_dev, void *cuda_stream) {
   if (count > 0 && !out_dev) return HSGA_ERR_INVALID_ARG;
-  if (policy > HSGA_NONE || !power_of_two(S) || S < 2 || S > 64) return HSGA_ERR_INVALID_ARG;
+  if (policy > HSGA_HYBRID || !power_of_two(S) || S < 2 || S > 64) return HSGA_ERR_INVALID_ARG;
+  if (policy == HSGA_HYBRID && S < 4) return HSGA_ERR_INVALID_ARG;
   if ((policy == HSGA_TILTED || policy == HSGA_STRETCHED) && (!power_of_two(W) || S / W < 2))
     return HSGA_ERR_INVALID_ARG;
   if (T0 + count >= 0xFFFFFFFFull) return HSGA_ERR_INVALID_ARG;

@@ -85,6 +85,15 @@ __host__ __device__ __forceinline__ uint32_t ctz64(uint64_t x) {  // x > 0
 // Site of deposition T; S = discard.  See hsga.h for the readings.
 __host__ __device__ __forceinline__ uint32_t site_of(uint32_t policy, uint32_t S, uint32_t W,
                                                      uint64_t T) {
+  if (policy == HSGA_HYBRID) {  // its steady half (sites [0, S/2))
+    S >>= 1;
+    policy = HSGA_STEADY;
+    const uint64_t t1 = T + 1;
+    const uint32_t s = bitlen64(S) - 1;
+    const uint32_t e = (t1 <= S) ? 0u : bitlen64(T) - s;
+    if (ctz64(t1) < e) return 2 * S;
+    return (uint32_t)(t1 % ((uint64_t)S + 1)) - 1u;
+  }
   const uint64_t t1 = T + 1;
   switch (policy) {
     case HSGA_TRIVIAL:
@@ -153,6 +162,7 @@ struct RunParams {
   uint32_t k0, k1;         // Philox key = seed
   uint32_t policy, S, W, bits;
   uint32_t interval;
+  uint32_t coarsen;        // annotate every coarsen-th generation (>= 1)
   // a5 thresholds floor(p 2^32) in [0, 2^32]: w2 < thr is (w2 < thr32) || thr_all
   uint32_t ben32, ben_all;  // beneficial: w2 < floor(p_ben 2^32)
   uint32_t bd32, bd_all;    // deleterious: otherwise w2 < floor(p_ben 2^32) + floor(p_del 2^32)
@@ -190,36 +200,68 @@ __device__ __forceinline__ Words4 philox_rk(const RunParams &p, uint32_t c0, uin
 }
 
 // Per-generation deposit parameters: a whole synchronous generation shares
-// T, hence the site.  The b-bit field never straddles the two 32-bit halves
-// of the surface (b divides 32), so the insert is one bit-select per half:
-// half = (half & clear) | ((w3 << shift) & ~clear), with clear = all ones for
-// the half not written (or for a discarded deposition).
+// T, hence the site.  A b-bit field never straddles the two 32-bit halves
+// of the surface (b divides 32), so each insert is one bit-select per half:
+// half = (half & clear) | ((value << shift) & ~clear), with clear = all ones
+// for a half not written (or a discarded deposition).  The hybrid policy has
+// a second field (its tilted half) whose value is bits 16.. of w3.
 struct Deposit {
-  uint32_t clear_lo, clear_hi;  // bits of each half kept from the parent
-  uint32_t shift;               // (site * b) mod 32
+  uint32_t clear_lo, clear_hi, shift;     // first field
+  uint32_t two;                           // a second field is written
+  uint32_t clear2_lo, clear2_hi, shift2;  // second field
 };
 
-__host__ __device__ __forceinline__ Deposit deposit_from_bit(uint32_t on, uint32_t bit,
-                                                             uint32_t vmask) {
+// Packed form: bits 0-5 bit offset of the first field, bit 6 "first field
+// written", bits 8-13 / 14 the same for the second field.
+constexpr uint32_t kPackOn = 0x40u;
+
+__host__ __device__ __forceinline__ uint32_t deposit_pack(const RunParams &p, uint64_t G) {
+  if (p.policy == HSGA_NONE) return 0u;
+  const uint32_t k = p.coarsen;
+  if (k > 1 && (G % k) != 0) return 0u;
+  const uint64_t T = k > 1 ? G / k : G;
+  uint32_t pack = 0u;
+  const uint32_t a = site_of(p.policy, p.S, p.W, T);
+  if (a < p.S) pack |= (a * p.bits) | kPackOn;
+  if (p.policy == HSGA_HYBRID) {
+    const uint32_t half = p.S / 2;
+    const uint32_t b = site_of(HSGA_TILTED, half, p.W, T);
+    if (b < half) pack |= (((half + b) * p.bits) | kPackOn) << 8;
+  }
+  return pack;
+}
+
+__host__ __device__ __forceinline__ Deposit deposit_unpack(uint32_t pack, uint32_t vmask) {
   Deposit d;
+  const uint32_t bit = pack & 63u, bit2 = (pack >> 8) & 63u;
+  const uint32_t field = (pack & kPackOn) ? (vmask << (bit & 31u)) : 0u;
+  const uint32_t field2 = ((pack >> 8) & kPackOn) ? (vmask << (bit2 & 31u)) : 0u;
   d.shift = bit & 31u;
-  const uint32_t field = on ? (vmask << d.shift) : 0u;
   d.clear_lo = (bit >> 5) ? 0xFFFFFFFFu : ~field;
   d.clear_hi = (bit >> 5) ? ~field : 0xFFFFFFFFu;
+  d.two = field2 != 0u;
+  d.shift2 = bit2 & 31u;
+  d.clear2_lo = (bit2 >> 5) ? 0xFFFFFFFFu : ~field2;
+  d.clear2_hi = (bit2 >> 5) ? ~field2 : 0xFFFFFFFFu;
   return d;
 }
 
-__host__ __device__ __forceinline__ Deposit deposit_for(const RunParams &p, uint64_t T) {
-  if (p.policy == HSGA_NONE) return deposit_from_bit(0u, 0u, (uint32_t)p.vmask);
-  const uint32_t site = site_of(p.policy, p.S, p.W, T);
-  if (site >= p.S) return deposit_from_bit(0u, 0u, (uint32_t)p.vmask);
-  return deposit_from_bit(1u, site * p.bits, (uint32_t)p.vmask);
+__host__ __device__ __forceinline__ Deposit deposit_for(const RunParams &p, uint64_t G) {
+  return deposit_unpack(deposit_pack(p, G), (uint32_t)p.vmask);
 }
 
+// TWO: the caller has checked that a second field is written (the check is
+// hoisted out of the per-agent code).
+template <bool TWO>
 __device__ __forceinline__ uint64_t deposit_into(const Deposit &d, uint64_t s, uint32_t w3) {
   const uint32_t v = w3 << d.shift;
-  const uint32_t lo = ((uint32_t)s & d.clear_lo) | (v & ~d.clear_lo);
-  const uint32_t hi = ((uint32_t)(s >> 32) & d.clear_hi) | (v & ~d.clear_hi);
+  uint32_t lo = ((uint32_t)s & d.clear_lo) | (v & ~d.clear_lo);
+  uint32_t hi = ((uint32_t)(s >> 32) & d.clear_hi) | (v & ~d.clear_hi);
+  if constexpr (TWO) {
+    const uint32_t v2 = (w3 >> 16) << d.shift2;
+    lo = (lo & d.clear2_lo) | (v2 & ~d.clear2_lo);
+    hi = (hi & d.clear2_hi) | (v2 & ~d.clear2_hi);
+  }
   return ((uint64_t)hi << 32) | lo;
 }
 

@@ -52,7 +52,7 @@ __device__ __forceinline__ void replication_words(const RunParams &p, uint32_t i
 // runs the same shuffles; children of lanes at or beyond n are garbage and
 // are never stored.  Candidate indices are always < n, so only loaded
 // parents are ever read.  T2: the tournament size is exactly 2.
-template <int AP, bool TRACKED, bool T2 = false, bool RK = true>
+template <int AP, bool TRACKED, bool T2 = false, bool RK = true, bool TWO = false>
 __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep, uint32_t isl,
                                           uint32_t G, const Words4 (&w)[AP],
                                           const uint32_t (&pt)[AP], const uint64_t (&ps)[AP],
@@ -92,7 +92,7 @@ __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep
     // a5: mutation of the winner's trait.
     ct[a] = mutate(p, fbest, w[a].z);
     // a6: the child inherits the winner's surface plus one new differentia.
-    if constexpr (TRACKED) cs[a] = deposit_into(dep, fetch64<AP>(ps, best), w[a].w);
+    if constexpr (TRACKED) cs[a] = deposit_into<TWO>(dep, fetch64<AP>(ps, best), w[a].w);
     else cs[a] = 0;
   }
 }
@@ -237,7 +237,8 @@ __device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
 // parallelism hides the multiply-xor dependency chain of the rounds).
 constexpr int kInterleave = 2;
 
-template <int AP, bool TRACKED, bool T2, int NN, int ILV = kInterleave, bool RK = true>
+template <int AP, bool TRACKED, bool T2, int NN, int ILV = kInterleave, bool RK = true,
+          bool TWO = false>
 __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &dep, uint32_t G,
                                            bool do_mig, uint32_t isl0,
                                            const uint32_t *__restrict__ tin,
@@ -265,8 +266,8 @@ __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &de
     uint64_t cs[ILV][AP];
 #pragma unroll
     for (int i = 0; i < ILV; ++i)
-      replicate<AP, TRACKED, T2, RK>(p, dep, isl0 + k + i, G, w[i], pt[k + i], ps[k + i],
-                                     ct[i], cs[i]);
+      replicate<AP, TRACKED, T2, RK, TWO>(p, dep, isl0 + k + i, G, w[i], pt[k + i],
+                                          ps[k + i], ct[i], cs[i]);
 #pragma unroll
     for (int i = 0; i < ILV; ++i)
       store_island<AP, TRACKED, NN>(p, isl0 + k + i, tout, sout, ct[i], cs[i]);
@@ -290,7 +291,8 @@ __device__ __noinline__ void partial_group(const RunParams &p, const Deposit &de
     Words4 w[AP];
     replication_words<AP, RK>(p, isl0 + k, G, w);
     if (do_mig) group_land<AP, TRACKED>(gm, k, pt, ps);
-    replicate<AP, TRACKED, T2, RK>(p, dep, isl0 + k, G, w, pt, ps, ct, cs);
+    if (dep.two) replicate<AP, TRACKED, T2, RK, true>(p, dep, isl0 + k, G, w, pt, ps, ct, cs);
+    else replicate<AP, TRACKED, T2, RK, false>(p, dep, isl0 + k, G, w, pt, ps, ct, cs);
     store_island<AP, TRACKED>(p, isl0 + k, tout, sout, ct, cs);
   }
 }

@@ -28,8 +28,13 @@ __global__ void __launch_bounds__(kStreamThreads)
   const uint32_t ngroups = (p.islands + kGroup - 1) / kGroup;
   for (uint32_t grp = blockIdx.x * wpb + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
     const uint32_t isl0 = grp * kGroup;
-    if (isl0 + kGroup <= p.islands)
-      full_group<AP, TRACKED, T2, NN>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
+    if (isl0 + kGroup <= p.islands) {
+      if (dep.two)
+        full_group<AP, TRACKED, T2, NN, kInterleave, true, true>(p, dep, G, do_mig != 0, isl0,
+                                                                 tin, sin, tout, sout);
+      else
+        full_group<AP, TRACKED, T2, NN>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
+    }
     else
       partial_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
   }

@@ -91,13 +91,9 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
   for (uint32_t g0 = 0; g0 < ngen && !failed; g0 += kChunk) {
     // Batched per-chunk draws: lane o (< 16) holds the emigrant block of
     // generation G0+g0+o, lane 16+o its placement block; every lane holds
-    // the deposit of generation G0+g0+(lane & 15), packed as site*b | on<<8.
+    // the packed deposit of generation G0+g0+(lane & 15).
     const uint32_t Gl = G0 + g0 + (lane & (kChunk - 1));
-    uint32_t dpack = 0u;
-    if (p.policy != HSGA_NONE) {
-      const uint32_t site = site_of(p.policy, p.S, p.W, Gl);
-      if (site < p.S) dpack = (site * p.bits) | 0x100u;
-    }
+    const uint32_t dpack = deposit_pack(p, Gl);
     Words4 mig[IPW];
 #pragma unroll
     for (int k = 0; k < IPW; ++k) {
@@ -110,7 +106,7 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
     for (uint32_t o = 0; o < steps; ++o) {
       const uint32_t G = G0 + g0 + o;
       const uint32_t dp = __shfl_sync(kFull, dpack, o);
-      const Deposit dep = deposit_from_bit(dp >> 8, dp & 0xFFu, (uint32_t)p.vmask);
+      const Deposit dep = deposit_unpack(dp, (uint32_t)p.vmask);
       const bool do_mig = migrates(p, G) && !(premigrated && g0 + o == 0);
       uint32_t buf = 0, seq = 0;
       if (do_mig) {
@@ -187,7 +183,9 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
         }
         uint32_t ct[AP];
         uint64_t cs[AP];
-        replicate<AP, TRACKED>(p, dep, isl[k], G, w, pt[k], ps[k], ct, cs);
+        if (dep.two) replicate<AP, TRACKED, false, true, true>(p, dep, isl[k], G, w, pt[k], ps[k],
+                                                               ct, cs);
+        else replicate<AP, TRACKED>(p, dep, isl[k], G, w, pt[k], ps[k], ct, cs);
 #pragma unroll
         for (int a = 0; a < AP; ++a) {
           pt[k][a] = ct[a];

@@ -30,9 +30,11 @@ def mixed_runs(seed, count):
         out.append((int(rng.integers(40, 400)),
                     dict(rows=rows, cols=cols, n=int(rng.integers(16, 65)),
                          tournament=int(rng.choice([1, 2, 2, 5])),
-                         policy=str(rng.choice(["steady", "tilted", "stretched", "trivial", "none"])),
+                         policy=str(rng.choice(["steady", "tilted", "stretched", "trivial", "none",
+                                                "hybrid"])),
                          bits=int(rng.choice([1, 2, 4])), p_ben=float(rng.choice([0.0, 1e-3, 0.05])),
                          p_del=float(rng.choice([0.0, 0.02])), interval=int(rng.choice([1, 1, 2, 0])),
+                         coarsen=int(rng.choice([1, 1, 3])),
                          seed=int(rng.integers(1, 2**40)))))
     return out
 

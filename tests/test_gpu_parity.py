@@ -40,7 +40,7 @@ def oracle_cfg(orc, kw):
                       tournament=kw.get("tournament", 2), policy=pol, bits=kw.get("bits", 1),
                       W=kw.get("W", 2), interval=kw.get("interval", 1),
                       p_ben=kw.get("p_ben", 0.0), p_del=kw.get("p_del", 0.0),
-                      seed=kw.get("seed", 1))
+                      seed=kw.get("seed", 1), coarsen=kw.get("coarsen", 1))
 
 
 def gpu_run(hb, kw, kernel, trait=None, surf=None, G0=0, chunks=(1,)):
@@ -103,6 +103,10 @@ EDGE = [
          p_del=0.1),
     dict(rows=9, cols=11, n=31, tournament=4, policy="tilted", bits=4, W=2, p_ben=0.5, p_del=0.5),
     dict(rows=2, cols=3, n=40, tournament=2, policy="steady", bits=1, p_del=1.0),
+    dict(rows=6, cols=7, n=32, tournament=2, policy="hybrid", bits=1, W=2, p_ben=0.01),
+    dict(rows=5, cols=5, n=20, tournament=3, policy="hybrid", bits=2, W=4, coarsen=3),
+    dict(rows=4, cols=9, n=32, tournament=2, policy="tilted", bits=1, coarsen=5, p_ben=0.02),
+    dict(rows=3, cols=3, n=64, tournament=2, policy="steady", bits=4, coarsen=2, interval=2),
 ]
 
 
