@@ -121,6 +121,8 @@ typedef struct hsga_stats {
   uint32_t islands_per_warp;    /* resident kernel tile shape (0 if streamed) */
   uint32_t warps_per_block;
   uint32_t blocks;
+  uint32_t fossils;             /* fossil records held */
+  uint64_t fossils_dropped;     /* fossil records not taken: buffer full */
 } hsga_stats;
 
 typedef struct hsga_grid hsga_grid;
@@ -175,6 +177,23 @@ int hsga_migrate(hsga_grid *g);
  * "On-hardware Trial"). */
 int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
                          uint32_t *out_island_slot);
+
+/* Fossil sampling (section "Distributed Phylogenetic Tracking": sampling
+ * genomes during the run keeps lineages that later go extinct in the
+ * reconstruction).  After every generation G that `every` divides,
+ * hsga_run_generations takes step a7 (k genomes, same draws and record
+ * layout as hsga_sample_surfaces at that G; word 3 holds G) into a device
+ * buffer of `capacity` records; once full, further samples are counted in
+ * hsga_stats.fossils_dropped.  every = 0 turns sampling off and frees the
+ * buffer; any call clears the records held.  k <= rows*cols,
+ * capacity >= k. */
+int hsga_set_fossil_sampling(hsga_grid *g, uint64_t every, uint32_t k, uint32_t capacity);
+
+/* Copies up to max_records fossil records (in sampling order) to out_words
+ * (4 words each) and out_island_slot (2 words each, may be NULL), host or
+ * device; *count receives the number of records held.  Synchronous. */
+int hsga_get_fossils(hsga_grid *g, uint32_t *out_words, uint32_t *out_island_slot,
+                     uint32_t max_records, uint32_t *count);
 
 /* Waits for the grid's stream and returns the first error a kernel reported
  * (HSGA_ERR_WAIT_TIMEOUT, HSGA_ERR_DEVICE) or a pending CUDA error. */

@@ -47,7 +47,8 @@ class hsga_stats(ctypes.Structure):
     _fields_ = [("generation", ctypes.c_uint64), ("replications", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
                 ("islands_per_warp", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
-                ("blocks", ctypes.c_uint32)]
+                ("blocks", ctypes.c_uint32), ("fossils", ctypes.c_uint32),
+                ("fossils_dropped", ctypes.c_uint64)]
 
 
 class hsga_batch_run_info(ctypes.Structure):
@@ -80,6 +81,10 @@ _SIGS = {
     "hsga_migrate": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_sample_surfaces": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                               ctypes.c_void_p], ctypes.c_int),
+    "hsga_set_fossil_sampling": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                  ctypes.c_uint32], ctypes.c_int),
+    "hsga_get_fossils": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                          ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "hsga_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_stats)], ctypes.c_int),
     "hsga_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
@@ -220,6 +225,22 @@ def hsga_migrate(g):
 def hsga_sample_surfaces(g, k: int, out_words, out_island_slot=None):
     _check(lib().hsga_sample_surfaces(g, int(k), _ptr(out_words), _ptr(out_island_slot)),
            "hsga_sample_surfaces")
+
+
+def hsga_set_fossil_sampling(g, every: int, k: int, capacity: int):
+    _check(lib().hsga_set_fossil_sampling(g, int(every), int(k), int(capacity)),
+           "hsga_set_fossil_sampling")
+
+
+def hsga_get_fossils(g, max_records: int):
+    """(words (n, 4), island/slot (n, 2)) of the fossil records held."""
+    words = np.zeros((max(1, max_records), 4), dtype=np.uint32)
+    where = np.zeros((max(1, max_records), 2), dtype=np.uint32)
+    cnt = ctypes.c_uint32()
+    _check(lib().hsga_get_fossils(g, _ptr(words), _ptr(where), int(max_records),
+                                  ctypes.byref(cnt)), "hsga_get_fossils")
+    m = min(cnt.value, max_records)
+    return words[:m], where[:m]
 
 
 def hsga_synchronize(g):

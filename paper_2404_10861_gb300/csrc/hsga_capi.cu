@@ -41,6 +41,12 @@ struct hsga_grid {
   int *err = nullptr;        // device error word
   uint32_t *sample_scratch = nullptr;
   size_t sample_scratch_bytes = 0;
+  // fossil sampling: k genomes every `fossil_every` generations
+  uint64_t fossil_every = 0;
+  uint32_t fossil_k = 0, fossil_cap = 0, fossil_count = 0;
+  uint64_t fossil_dropped = 0;
+  uint32_t *fossil_words = nullptr;  // fossil_cap x 4
+  uint32_t *fossil_where = nullptr;  // fossil_cap x 2
   uint64_t G = 0;
   bool premigrated = false;
   bool resident = false;
@@ -166,6 +172,8 @@ void free_grid(hsga_grid *g) {
   dev_free(g->alloc, g->flags, g->stream);
   dev_free(g->alloc, g->err, g->stream);
   dev_free(g->alloc, g->sample_scratch, g->stream);
+  dev_free(g->alloc, g->fossil_words, g->stream);
+  dev_free(g->alloc, g->fossil_where, g->stream);
   cudaStreamSynchronize(g->stream);
   delete g;
 }
@@ -296,11 +304,64 @@ int hsga_get_population(hsga_grid *g, uint32_t *trait, uint64_t *surf) {
   return HSGA_OK;
 }
 
+namespace {
+
+int ensure_sample_scratch(hsga_grid *g, uint32_t k) {
+  const size_t scratch = sample_scratch_bytes(g->p, k);
+  if (scratch > g->sample_scratch_bytes) {
+    dev_free(g->alloc, g->sample_scratch, g->stream);
+    g->sample_scratch = (uint32_t *)dev_alloc(g->alloc, scratch, g->stream);
+    g->sample_scratch_bytes = g->sample_scratch ? scratch : 0;
+    if (!g->sample_scratch) return HSGA_ERR_OOM;
+  }
+  return HSGA_OK;
+}
+
+int advance(hsga_grid *g, uint64_t n);
+
+// One fossil sample at the current generation into the fossil buffer.
+int take_fossils(hsga_grid *g) {
+  if (g->fossil_count + g->fossil_k > g->fossil_cap) {
+    g->fossil_dropped += g->fossil_k;
+    return HSGA_OK;
+  }
+  const int r = ensure_sample_scratch(g, g->fossil_k);
+  if (r != HSGA_OK) return r;
+  cudaError_t e = launch_sample(g->p, (uint32_t)g->G, g->fossil_k, g->trait[g->cur],
+                                g->surf[g->cur], g->fossil_words + 4 * (size_t)g->fossil_count,
+                                g->fossil_where + 2 * (size_t)g->fossil_count, g->sample_scratch,
+                                g->stream);
+  g->launches++;
+  g->fossil_count += g->fossil_k;
+  return cuda_status(e);
+}
+
+}  // namespace
+
 int hsga_run_generations(hsga_grid *g, uint64_t n) {
   if (!g) return HSGA_ERR_INVALID_ARG;
   if (g->broken) return HSGA_ERR_DEVICE;
   if (n == 0) return HSGA_OK;
   if (g->G + n > kMaxGeneration) return HSGA_ERR_INVALID_ARG;
+  if (!g->fossil_every) return advance(g, n);
+  // stop at every multiple of the fossil interval to sample
+  uint64_t left = n;
+  while (left > 0) {
+    const uint64_t to_next = g->fossil_every - (g->G % g->fossil_every);
+    const uint64_t step = left < to_next ? left : to_next;
+    int r = advance(g, step);
+    if (r != HSGA_OK) return r;
+    left -= step;
+    if (g->G % g->fossil_every == 0) {
+      r = take_fossils(g);
+      if (r != HSGA_OK) return r;
+    }
+  }
+  return HSGA_OK;
+}
+
+namespace {
+int advance(hsga_grid *g, uint64_t n) {
   cudaError_t e = cudaSuccess;
   if (g->resident) {
     // Launch in slices so a single launch stays short.
@@ -330,6 +391,49 @@ int hsga_run_generations(hsga_grid *g, uint64_t n) {
   g->replications += n * g->agents;
   return HSGA_OK;
 }
+}  // namespace
+
+int hsga_set_fossil_sampling(hsga_grid *g, uint64_t every, uint32_t k, uint32_t capacity) {
+  if (!g) return HSGA_ERR_INVALID_ARG;
+  if (every && (k == 0 || k > g->p.islands || capacity < k)) return HSGA_ERR_INVALID_ARG;
+  dev_free(g->alloc, g->fossil_words, g->stream);
+  dev_free(g->alloc, g->fossil_where, g->stream);
+  g->fossil_words = g->fossil_where = nullptr;
+  g->fossil_every = 0;
+  g->fossil_k = g->fossil_cap = g->fossil_count = 0;
+  g->fossil_dropped = 0;
+  if (!every) return HSGA_OK;
+  g->fossil_words = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * 4 * (size_t)capacity,
+                                          g->stream);
+  g->fossil_where = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * 2 * (size_t)capacity,
+                                          g->stream);
+  if (!g->fossil_words || !g->fossil_where) {
+    dev_free(g->alloc, g->fossil_words, g->stream);
+    dev_free(g->alloc, g->fossil_where, g->stream);
+    g->fossil_words = g->fossil_where = nullptr;
+    return HSGA_ERR_OOM;
+  }
+  g->fossil_every = every;
+  g->fossil_k = k;
+  g->fossil_cap = capacity;
+  return HSGA_OK;
+}
+
+int hsga_get_fossils(hsga_grid *g, uint32_t *out_words, uint32_t *out_island_slot,
+                     uint32_t max_records, uint32_t *count) {
+  if (!g || !count) return HSGA_ERR_INVALID_ARG;
+  *count = g->fossil_count;
+  const uint32_t m = g->fossil_count < max_records ? g->fossil_count : max_records;
+  if (m == 0) return HSGA_OK;
+  if (!out_words) return HSGA_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(out_words, g->fossil_words, sizeof(uint32_t) * 4 * (size_t)m,
+                                  cudaMemcpyDefault, g->stream);
+  if (e == cudaSuccess && out_island_slot)
+    e = cudaMemcpyAsync(out_island_slot, g->fossil_where, sizeof(uint32_t) * 2 * (size_t)m,
+                        cudaMemcpyDefault, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  return cuda_status(e);
+}
 
 int hsga_migrate(hsga_grid *g) {
   if (!g) return HSGA_ERR_INVALID_ARG;
@@ -348,13 +452,8 @@ int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
   if (!g || (k > 0 && !out_words)) return HSGA_ERR_INVALID_ARG;
   if (k > g->p.islands) return HSGA_ERR_INVALID_ARG;
   if (k == 0) return HSGA_OK;
-  const size_t scratch = sample_scratch_bytes(g->p, k);
-  if (scratch > g->sample_scratch_bytes) {
-    dev_free(g->alloc, g->sample_scratch, g->stream);
-    g->sample_scratch = (uint32_t *)dev_alloc(g->alloc, scratch, g->stream);
-    g->sample_scratch_bytes = g->sample_scratch ? scratch : 0;
-    if (!g->sample_scratch) return HSGA_ERR_OOM;
-  }
+  const int sr = ensure_sample_scratch(g, k);
+  if (sr != HSGA_OK) return sr;
   // the kernels store 16-byte records and 8-byte pairs: misaligned device
   // outputs go through the staging buffer like host outputs
   const bool dev_words = is_device_ptr(out_words) && ((uintptr_t)out_words % 16) == 0;
@@ -406,6 +505,8 @@ int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
     out->warps_per_block = (uint32_t)g->plan.warps_per_block;
     out->blocks = (uint32_t)g->plan.blocks;
   }
+  out->fossils = g->fossil_count;
+  out->fossils_dropped = g->fossil_dropped;
   return HSGA_OK;
 }
 
