@@ -123,6 +123,8 @@ def lib():
         _lib.orc_sample_grid.argtypes = [P(_Cfg), P(u32), P(u64), u64, u32, P(u32),
                                          ctypes.c_void_p]
         _lib.orc_sample_grid.restype = ctypes.c_int
+        _lib.orc_run_async.argtypes = [P(_Cfg), P(u32), P(u64), P(u32), u64, u32, P(u32)]
+        _lib.orc_run_async.restype = ctypes.c_int
     return _lib
 
 
@@ -239,6 +241,51 @@ def sample(cfg: Config, trait, surf, G: int, k: int):
     if rc != 0:
         raise MemoryError("oracle sample failed")
     return words, where
+
+
+# ------------------------------------------------- free-running migration ---
+
+def run_async(cfg: Config, trait, surf, tcount, G0: int, generations: int, schedule):
+    """Free-running migration replayed from a schedule (see hsga_oracle.c):
+    schedule[island, g, d] = 1 + the neighbour generation whose emigrant the
+    island took from direction d at its generation g (0 = none).  Genomes
+    carry their own deposition counters ``tcount``.  Returns (trait, surf,
+    tcount)."""
+    trait = np.ascontiguousarray(trait, dtype=np.uint32).copy()
+    surf = np.ascontiguousarray(surf, dtype=np.uint64).copy()
+    tcount = np.ascontiguousarray(tcount, dtype=np.uint32).copy()
+    sched = np.ascontiguousarray(schedule, dtype=np.uint32).reshape(-1)
+    if sched.size != cfg.islands * generations * 4:
+        raise ValueError("schedule must be islands x generations x 4")
+    c = cfg._c()
+    rc = lib().orc_run_async(ctypes.byref(c), _p(trait, ctypes.c_uint32),
+                             _p(surf, ctypes.c_uint64), _p(tcount, ctypes.c_uint32), G0,
+                             generations, _p(sched, ctypes.c_uint32))
+    if rc == -3:
+        raise ValueError("schedule inconsistent with the emigrants' directions or causality")
+    if rc != 0:
+        raise MemoryError("oracle async run failed")
+    return trait, surf, tcount
+
+
+def sync_schedule(cfg: Config, G0: int, generations: int) -> np.ndarray:
+    """The schedule under which free-running migration reproduces the
+    synchronous run: at generation g every island takes, from each neighbour,
+    that neighbour's generation-g emigrant if it was aimed at the island."""
+    I = cfg.islands
+    out = np.zeros((I, generations, 4), dtype=np.uint32)
+    for g in range(generations):
+        G = G0 + g
+        if not (cfg.interval > 0 and G % cfg.interval == 0):
+            continue
+        dirs = np.array([int(philox4x32((cfg.seed & 0xFFFFFFFF, cfg.seed >> 32),
+                                        (0xFFFFFFFF, i, G, 0))[1]) >> 30 for i in range(I)])
+        for i in range(I):
+            for d in range(4):
+                nb = neighbour(cfg, i, d)
+                if dirs[nb] == (d + 2) % 4:
+                    out[i, g, d] = g + 1
+    return out
 
 
 # ------------------------------------------- pieces for band decomposition ---

@@ -524,3 +524,149 @@ int orc_sample_grid(const orc_cfg *cfg, const uint32_t *trait,
   free(perm);
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Free-running (asynchronous) migration, replayed from a schedule.
+ *
+ * The paper's WSE islands run without a global clock: each keeps one
+ * outgoing emigrant buffer per neighbour and takes whatever its neighbours
+ * last sent ("Methods › Asynchronous Island-model Genetic Algorithm").  Here
+ * every island publishes one emigrant per generation (slot and direction
+ * from Philox(key; 0xFFFFFFFF, island, G, 0), as in synchronous mode), and
+ * at each of its generations may take, from each neighbour, the latest
+ * emigrant that neighbour aimed at it.  Which neighbour generation each
+ * accepted emigrant came from is a property of the run's timing, so it is an
+ * input: sched[(island * n_gens + g) * 4 + d] = 1 + the neighbour's
+ * generation whose emigrant island `island` took from direction d at its own
+ * generation g (relative to G0), or 0 for none.  Genomes carry their own
+ * deposition counter T (the paper's per-genome generation counter): an
+ * immigrant keeps its T, and a child deposits at site_fn(T_parent) and
+ * carries T_parent + 1.  Given the schedule the run is deterministic.
+ *
+ * trait, surf, tcount: the population at G0 (updated in place).  Returns 0,
+ * -1 on allocation failure, -3 if the schedule names an emigrant that was not
+ * aimed at the island or cannot be ordered causally. */
+int orc_run_async(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
+                  uint32_t *tcount, uint64_t G0, uint32_t n_gens,
+                  const uint32_t *sched) {
+  uint32_t I = cfg->rows * cfg->cols, n = cfg->n;
+  uint32_t S = 64 / cfg->bits;
+  uint64_t vmask = (1ull << cfg->bits) - 1;
+  uint64_t thr_b = orc_threshold(cfg->p_ben), thr_d = orc_threshold(cfg->p_del);
+  /* emigrant records by island and generation: trait, lo, hi, T, dir */
+  uint32_t *hist = malloc(sizeof(uint32_t) * 5 * (size_t)I * (n_gens + 1));
+  uint32_t *done = calloc(I, sizeof(uint32_t));
+  uint32_t *ct = malloc(sizeof(uint32_t) * n), *cT = malloc(sizeof(uint32_t) * n);
+  uint64_t *cs = malloc(sizeof(uint64_t) * n);
+  if (!hist || !done || !ct || !cT || !cs) {
+    free(hist); free(done); free(ct); free(cT); free(cs);
+    return -1;
+  }
+  /* the emigrant each island publishes at the start of its generation g */
+#define ORC_PUBLISH(I_, G_)                                                    \
+  do {                                                                         \
+    uint32_t w_[4];                                                            \
+    orc_draw(cfg->seed, 0xFFFFFFFFu, (I_), (uint32_t)(G0 + (G_)), 0, w_);      \
+    size_t a_ = (size_t)(I_) * n + orc_index(w_[0], n);                        \
+    uint32_t *h_ = hist + 5 * ((size_t)(I_) * (n_gens + 1) + (G_));            \
+    h_[0] = trait[a_];                                                         \
+    h_[1] = (uint32_t)surf[a_];                                                \
+    h_[2] = (uint32_t)(surf[a_] >> 32);                                        \
+    h_[3] = tcount[a_];                                                        \
+    h_[4] = w_[1] >> 30;                                                       \
+  } while (0)
+  for (uint32_t i = 0; i < I; ++i) ORC_PUBLISH(i, 0);
+  int status = 0;
+  uint64_t remaining = (uint64_t)I * n_gens;
+  while (remaining > 0 && status == 0) {
+    int progress = 0;
+    for (uint32_t i = 0; i < I && status == 0; ++i) {
+      uint32_t g = done[i];
+      if (g >= n_gens) continue;
+      uint64_t G = G0 + g;
+      const uint32_t *req = sched + ((size_t)i * n_gens + g) * 4;
+      int ready = 1;
+      for (uint32_t d = 0; d < 4; ++d) {
+        if (!req[d]) continue;
+        uint32_t nb = orc_neighbour(cfg, i, d);
+        if (req[d] - 1 > n_gens || done[nb] < req[d] - 1) ready = 0;
+      }
+      if (!ready) continue;
+      /* a2: take the scheduled emigrants, directions N, E, S, W */
+      if (orc_migrates(cfg, G)) {
+        uint32_t v[4];
+        orc_draw(cfg->seed, 0xFFFFFFFEu, i, (uint32_t)G, 0, v);
+        for (uint32_t d = 0; d < 4; ++d) {
+          if (!req[d]) continue;
+          uint32_t nb = orc_neighbour(cfg, i, d);
+          const uint32_t *h = hist + 5 * ((size_t)nb * (n_gens + 1) + (req[d] - 1));
+          if (h[4] != (d + 2) % 4) { status = -3; break; }
+          size_t a = (size_t)i * n + orc_index(v[d], n);
+          trait[a] = h[0];
+          surf[a] = (uint64_t)h[1] | ((uint64_t)h[2] << 32);
+          tcount[a] = h[3];
+        }
+      } else {
+        for (uint32_t d = 0; d < 4; ++d)
+          if (req[d]) status = -3;
+      }
+      if (status) break;
+      /* a3-a6 with per-genome counters */
+      const uint32_t *fit = trait + (size_t)i * n;
+      for (uint32_t j = 0; j < n; ++j) {
+        uint32_t w[4];
+        orc_draw(cfg->seed, j, i, (uint32_t)G, 1, w);
+        uint32_t best = orc_index(w[0], n);
+        for (uint32_t c = 1; c < cfg->tournament; ++c) {
+          uint32_t word;
+          if (c == 1) {
+            word = w[1];
+          } else {
+            uint32_t extra[4];
+            orc_draw(cfg->seed, j, i, (uint32_t)G, 2 + (c - 2) / 4, extra);
+            word = extra[(c - 2) % 4];
+          }
+          uint32_t cand = orc_index(word, n);
+          if (fit[cand] > fit[best]) best = cand;
+        }
+        size_t pa = (size_t)i * n + best;
+        uint32_t tr = trait[pa];
+        uint64_t su = surf[pa];
+        uint32_t T = tcount[pa];
+        if ((uint64_t)w[2] < thr_b) {
+          if (tr != 0xFFFFFFFFu) tr += 1;
+        } else if ((uint64_t)w[2] < thr_b + thr_d) {
+          if (tr != 0) tr -= 1;
+        }
+        if (cfg->policy != ORC_NONE) {
+          uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
+          if (site < S) {
+            su &= ~(vmask << (site * cfg->bits));
+            su |= ((uint64_t)w[3] & vmask) << (site * cfg->bits);
+          }
+          if (cfg->policy == ORC_HYBRID) {
+            uint32_t site2 = orc_hybrid_second_site(S, cfg->W, T);
+            if (site2 < S) {
+              su &= ~(vmask << (site2 * cfg->bits));
+              su |= ((uint64_t)(w[3] >> 16) & vmask) << (site2 * cfg->bits);
+            }
+          }
+        }
+        ct[j] = tr;
+        cs[j] = su;
+        cT[j] = T + 1;
+      }
+      memcpy(trait + (size_t)i * n, ct, sizeof(uint32_t) * n);
+      memcpy(surf + (size_t)i * n, cs, sizeof(uint64_t) * n);
+      memcpy(tcount + (size_t)i * n, cT, sizeof(uint32_t) * n);
+      done[i] = g + 1;
+      ORC_PUBLISH(i, g + 1);
+      --remaining;
+      progress = 1;
+    }
+    if (!progress && status == 0) status = -3;
+  }
+#undef ORC_PUBLISH
+  free(hist); free(done); free(ct); free(cT); free(cs);
+  return status;
+}
