@@ -95,6 +95,19 @@ typedef enum hsga_kernel {
   HSGA_KERNEL_RESIDENT_GRID = 3  /* resident, always the cooperative multi-block form */
 } hsga_kernel;
 
+/* Migration modes.  Synchronous: every island takes its neighbours' emigrants
+ * of the same generation (bit-reproducible).  Free-running: islands never
+ * wait for one another; each takes a neighbour's latest emigrant if it is new
+ * and aimed at it (the WSE's own regime, section "Asynchronous Island-model
+ * Genetic Algorithm"); results depend on timing, genomes carry their own
+ * deposition counters, and agents_per_island <= 32, deposit_interval <= 1.
+ * Free-running grids do not support hsga_migrate, checkpoints, batches or the
+ * allocation-free entry point. */
+typedef enum hsga_migration_mode {
+  HSGA_MIGRATION_SYNC = 0,
+  HSGA_MIGRATION_ASYNC = 1
+} hsga_migration_mode;
+
 /* Run configuration (plain data, caller-owned; copied by hsga_init_grid). */
 typedef struct hsga_config {
   uint32_t rows, cols;          /* toroidal island grid, each >= 1 */
@@ -111,6 +124,8 @@ typedef struct hsga_config {
   uint32_t deposit_interval;    /* temporal coarsening k: only generations G with
                                    k | G deposit, as deposition G / k (0 or 1:
                                    every generation) */
+  uint32_t migration_mode;      /* hsga_migration_mode */
+  uint32_t reserved;            /* must be 0 */
 } hsga_config;
 
 typedef struct hsga_stats {
@@ -194,6 +209,23 @@ int hsga_set_fossil_sampling(hsga_grid *g, uint64_t every, uint32_t k, uint32_t 
  * device; *count receives the number of records held.  Synchronous. */
 int hsga_get_fossils(hsga_grid *g, uint32_t *out_words, uint32_t *out_island_slot,
                      uint32_t max_records, uint32_t *count);
+
+/* Per-genome deposition counters T (rows*cols*n uint32, host or device).  In
+ * synchronous mode every genome's T is the generation.  Synchronous when the
+ * destination is host memory. */
+int hsga_get_counters(hsga_grid *g, uint32_t *T_out);
+
+/* Free-running grids: logs, for the next `generations` generations from the
+ * current one, which neighbour emigrant each island took: entry
+ * ((island * generations + g) * 4 + d) holds 1 + the absolute generation of
+ * the emigrant taken from direction d at generation G_now + g, or 0.  Starts
+ * a fresh free-running window (no record published earlier is taken), so the
+ * CPU oracle can replay the window exactly.  generations = 0 stops logging. */
+int hsga_set_async_log(hsga_grid *g, uint32_t generations);
+
+/* Copies the log (islands * generations * 4 uint32; host or device).
+ * Synchronous. */
+int hsga_get_async_log(hsga_grid *g, uint32_t *out);
 
 /* Waits for the grid's stream and returns the first error a kernel reported
  * (HSGA_ERR_WAIT_TIMEOUT, HSGA_ERR_DEVICE) or a pending CUDA error. */

@@ -40,7 +40,8 @@ class hsga_config(ctypes.Structure):
                 ("sites_per_level", ctypes.c_uint32), ("migration_interval", ctypes.c_uint32),
                 ("p_beneficial", ctypes.c_double), ("p_deleterious", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
-                ("deposit_interval", ctypes.c_uint32)]
+                ("deposit_interval", ctypes.c_uint32), ("migration_mode", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class hsga_stats(ctypes.Structure):
@@ -85,6 +86,9 @@ _SIGS = {
                                   ctypes.c_uint32], ctypes.c_int),
     "hsga_get_fossils": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                           ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "hsga_get_counters": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hsga_set_async_log": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "hsga_get_async_log": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "hsga_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_stats)], ctypes.c_int),
     "hsga_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
@@ -192,10 +196,10 @@ def use_default_allocator():
 # ------------------------------------------------------------ functions ---
 def make_config(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2,
                 interval=1, p_ben=0.0, p_del=0.0, seed=1, kernel=KERNEL_AUTO,
-                coarsen=1) -> hsga_config:
+                coarsen=1, mode="sync") -> hsga_config:
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return hsga_config(rows, cols, n, tournament, pol, bits, W, interval, p_ben, p_del,
-                       seed, kernel, coarsen)
+                       seed, kernel, coarsen, {"sync": 0, "async": 1}[mode], 0)
 
 
 def hsga_init_grid(cfg: hsga_config, cuda_stream=None) -> ctypes.c_void_p:
@@ -241,6 +245,20 @@ def hsga_get_fossils(g, max_records: int):
                                   ctypes.byref(cnt)), "hsga_get_fossils")
     m = min(cnt.value, max_records)
     return words[:m], where[:m]
+
+
+def hsga_get_counters(g, T_out):
+    _check(lib().hsga_get_counters(g, _ptr(T_out)), "hsga_get_counters")
+
+
+def hsga_set_async_log(g, generations: int):
+    _check(lib().hsga_set_async_log(g, int(generations)), "hsga_set_async_log")
+
+
+def hsga_get_async_log(g, islands: int, generations: int) -> np.ndarray:
+    out = np.zeros((islands, generations, 4), dtype=np.uint32)
+    _check(lib().hsga_get_async_log(g, _ptr(out)), "hsga_get_async_log")
+    return out
 
 
 def hsga_synchronize(g):
@@ -437,6 +455,11 @@ class Grid:
         s = np.zeros(self.agents, dtype=np.uint64)
         hsga_get_population(self.handle, t, s)
         return t, s
+
+    def counters(self):
+        T = np.zeros(self.agents, dtype=np.uint32)
+        hsga_get_counters(self.handle, T)
+        return T
 
     def run(self, n):
         hsga_run_generations(self.handle, n)

@@ -47,6 +47,14 @@ struct hsga_grid {
   uint64_t fossil_dropped = 0;
   uint32_t *fossil_words = nullptr;  // fossil_cap x 4
   uint32_t *fossil_where = nullptr;  // fossil_cap x 2
+  // free-running migration: per-genome counters, last stamp seen per
+  // (island, direction), optional take log
+  bool async = false;
+  uint32_t *tcount = nullptr;
+  uint32_t *seen = nullptr;
+  uint32_t *alog = nullptr;
+  uint32_t alog_gens = 0;
+  uint64_t alog_G0 = 0;
   uint64_t G = 0;
   bool premigrated = false;
   bool resident = false;
@@ -110,7 +118,11 @@ int validate(const hsga_config *c) {
   if (!(c->p_beneficial >= 0.0 && c->p_beneficial <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (!(c->p_deleterious >= 0.0 && c->p_deleterious <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
-  if (c->kernel > HSGA_KERNEL_RESIDENT_GRID) return HSGA_ERR_INVALID_ARG;
+  if (c->kernel > HSGA_KERNEL_RESIDENT_GRID || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
+  if (c->migration_mode > HSGA_MIGRATION_ASYNC) return HSGA_ERR_INVALID_ARG;
+  if (c->migration_mode == HSGA_MIGRATION_ASYNC &&
+      (c->agents_per_island > 32 || c->deposit_interval > 1))
+    return HSGA_ERR_INVALID_ARG;
   return HSGA_OK;
 }
 
@@ -174,6 +186,9 @@ void free_grid(hsga_grid *g) {
   dev_free(g->alloc, g->sample_scratch, g->stream);
   dev_free(g->alloc, g->fossil_words, g->stream);
   dev_free(g->alloc, g->fossil_where, g->stream);
+  dev_free(g->alloc, g->tcount, g->stream);
+  dev_free(g->alloc, g->seen, g->stream);
+  dev_free(g->alloc, g->alog, g->stream);
   cudaStreamSynchronize(g->stream);
   delete g;
 }
@@ -183,8 +198,23 @@ cudaError_t copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
 }
 
+__global__ void fill_u32_kernel(uint32_t *dst, uint32_t value, uint64_t count) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    dst[i] = value;
+}
+
+cudaError_t fill_u32(uint32_t *dst, uint32_t value, uint64_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const uint64_t blocks = (count + 255) / 256;
+  fill_u32_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(dst, value, count);
+  return cudaGetLastError();
+}
+
 int reset_sync_state(hsga_grid *g) {
   cudaError_t e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+  if (e == cudaSuccess && g->seen)
+    e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), g->stream);
   g->broken = false;
   g->premigrated = false;
@@ -237,6 +267,20 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
                          : nullptr;
   }
   g->rec = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
+  g->async = cfg->migration_mode == HSGA_MIGRATION_ASYNC;
+  if (g->async) {
+    g->tcount = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->agents, g->stream);
+    g->seen = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * 4 * (size_t)g->p.islands,
+                                    g->stream);
+    if (!g->tcount || !g->seen) {
+      free_grid(g);
+      return HSGA_ERR_OOM;
+    }
+    if (cudaMemsetAsync(g->tcount, 0, sizeof(uint32_t) * g->agents, g->stream) != cudaSuccess) {
+      free_grid(g);
+      return HSGA_ERR_CUDA;
+    }
+  }
   g->flags = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->p.islands, g->stream);
   g->err = (int *)dev_alloc(g->alloc, sizeof(int), g->stream);
   bool ok = g->trait[0] && g->trait[1] && g->rec && g->flags && g->err &&
@@ -255,7 +299,7 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
     return HSGA_ERR_CUDA;
   }
   g->resident = false;
-  if (cfg->kernel != HSGA_KERNEL_STREAMED) {
+  if (cfg->kernel != HSGA_KERNEL_STREAMED && !g->async) {
     g->resident = resident_plan(g->p, &g->plan, cfg->kernel == HSGA_KERNEL_RESIDENT_GRID);
     if (!g->resident && cfg->kernel >= HSGA_KERNEL_RESIDENT) {
       free_grid(g);
@@ -277,6 +321,8 @@ int hsga_set_population(hsga_grid *g, const uint32_t *trait, const uint64_t *sur
     e = copy_in(g->surf[0], surf, sizeof(uint64_t) * g->agents, g->stream);
   if (e != cudaSuccess) return HSGA_ERR_CUDA;
   g->G = generation;
+  if (g->async && fill_u32(g->tcount, (uint32_t)generation, g->agents, g->stream) != cudaSuccess)
+    return HSGA_ERR_CUDA;
   int r = reset_sync_state(g);
   if (r != HSGA_OK) return r;
   // host sources may be reused on return
@@ -330,7 +376,7 @@ int take_fossils(hsga_grid *g) {
   cudaError_t e = launch_sample(g->p, (uint32_t)g->G, g->fossil_k, g->trait[g->cur],
                                 g->surf[g->cur], g->fossil_words + 4 * (size_t)g->fossil_count,
                                 g->fossil_where + 2 * (size_t)g->fossil_count, g->sample_scratch,
-                                g->stream);
+                                g->stream, g->tcount);
   g->launches++;
   g->fossil_count += g->fossil_k;
   return cuda_status(e);
@@ -363,7 +409,17 @@ int hsga_run_generations(hsga_grid *g, uint64_t n) {
 namespace {
 int advance(hsga_grid *g, uint64_t n) {
   cudaError_t e = cudaSuccess;
-  if (g->resident) {
+  if (g->async) {
+    const uint64_t slice = 1u << 16;
+    for (uint64_t done = 0; done < n && e == cudaSuccess;) {
+      const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
+      e = launch_step_async(g->p, (uint32_t)(g->G + done), m, g->trait[g->cur], g->surf[g->cur],
+                            g->tcount, g->rec, g->flags, g->seen, g->alog,
+                            (uint32_t)g->alog_G0, g->alog_gens, g->stream);
+      g->launches++;
+      done += m;
+    }
+  } else if (g->resident) {
     // Launch in slices so a single launch stays short.
     const uint64_t slice = 1u << 16;
     uint64_t done = 0;
@@ -435,9 +491,58 @@ int hsga_get_fossils(hsga_grid *g, uint32_t *out_words, uint32_t *out_island_slo
   return cuda_status(e);
 }
 
+int hsga_get_counters(hsga_grid *g, uint32_t *T_out) {
+  if (!g || !T_out) return HSGA_ERR_INVALID_ARG;
+  cudaError_t e;
+  const bool dev = is_device_ptr(T_out);
+  if (g->async) {
+    e = cudaMemcpyAsync(T_out, g->tcount, sizeof(uint32_t) * g->agents, cudaMemcpyDefault,
+                        g->stream);
+  } else if (dev) {
+    e = fill_u32(T_out, (uint32_t)g->G, g->agents, g->stream);
+  } else {
+    for (uint64_t i = 0; i < g->agents; ++i) T_out[i] = (uint32_t)g->G;
+    e = cudaSuccess;
+  }
+  if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(g->stream);
+  return cuda_status(e);
+}
+
+int hsga_set_async_log(hsga_grid *g, uint32_t generations) {
+  if (!g) return HSGA_ERR_INVALID_ARG;
+  if (!g->async) return HSGA_ERR_UNSUPPORTED;
+  dev_free(g->alloc, g->alog, g->stream);
+  g->alog = nullptr;
+  g->alog_gens = 0;
+  if (!generations) return HSGA_OK;
+  const size_t bytes = sizeof(uint32_t) * 4 * (size_t)g->p.islands * generations;
+  g->alog = (uint32_t *)dev_alloc(g->alloc, bytes, g->stream);
+  if (!g->alog) return HSGA_ERR_OOM;
+  cudaError_t e = cudaMemsetAsync(g->alog, 0, bytes, g->stream);
+  // a fresh window: nothing published before it can be taken
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
+  g->alog_gens = generations;
+  g->alog_G0 = g->G;
+  return cuda_status(e);
+}
+
+int hsga_get_async_log(hsga_grid *g, uint32_t *out) {
+  if (!g || !out) return HSGA_ERR_INVALID_ARG;
+  if (!g->alog) return HSGA_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(out, g->alog,
+                                  sizeof(uint32_t) * 4 * (size_t)g->p.islands * g->alog_gens,
+                                  cudaMemcpyDefault, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  return cuda_status(e);
+}
+
 int hsga_migrate(hsga_grid *g) {
   if (!g) return HSGA_ERR_INVALID_ARG;
   if (g->broken) return HSGA_ERR_DEVICE;
+  if (g->async) return HSGA_ERR_UNSUPPORTED;
   if (g->premigrated) return HSGA_ERR_INVALID_ARG;
   cudaError_t e = launch_migrate(g->p, (uint32_t)g->G, g->trait[g->cur], g->surf[g->cur], g->rec,
                                  g->stream);
@@ -468,7 +573,7 @@ int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
     if (!dev_is) di = staging + 4 * (size_t)k;
   }
   cudaError_t e = launch_sample(g->p, (uint32_t)g->G, k, g->trait[g->cur], g->surf[g->cur], dw,
-                                di, g->sample_scratch, g->stream);
+                                di, g->sample_scratch, g->stream, g->tcount);
   g->launches++;
   if (e == cudaSuccess && !dev_words)
     e = cudaMemcpyAsync(out_words, dw, sizeof(uint32_t) * 4 * (size_t)k, cudaMemcpyDefault,
@@ -513,6 +618,7 @@ int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
 // Checkpoint layout: magic, config, G, then traits and surfaces.
 int hsga_save(hsga_grid *g, void *buf, size_t *len) {
   if (!g || !len) return HSGA_ERR_INVALID_ARG;
+  if (g->async) return HSGA_ERR_UNSUPPORTED;
   const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 12;
   if (!buf) {
     *len = need;
@@ -537,6 +643,7 @@ int hsga_save(hsga_grid *g, void *buf, size_t *len) {
 
 int hsga_load(hsga_grid *g, const void *buf, size_t len) {
   if (!g || !buf) return HSGA_ERR_INVALID_ARG;
+  if (g->async) return HSGA_ERR_UNSUPPORTED;
   const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 12;
   if (len < need) return HSGA_ERR_INVALID_ARG;
   const char *p = (const char *)buf;

@@ -41,9 +41,16 @@ cudaError_t launch_migrate(const RunParams &p, uint32_t G, uint32_t *t, uint64_t
 
 size_t sample_scratch_bytes(const RunParams &p, uint32_t k);
 
+// T: per-genome deposition counters (free-running grids) written as word 3,
+// or NULL to write G.
 cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint32_t *t,
                           const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
-                          uint32_t *scratch, cudaStream_t stream);
+                          uint32_t *scratch, cudaStream_t stream, const uint32_t *T = nullptr);
+
+cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t *t,
+                              uint64_t *s, uint32_t *T, uint4 *rec, uint32_t *stamp,
+                              uint32_t *seen, uint32_t *log, uint32_t log_G0, uint32_t log_gens,
+                              cudaStream_t stream);
 
 // Device memory through the registered allocator hooks (hsga_capi.cu).
 struct AllocHooks {

@@ -160,7 +160,8 @@ __device__ __forceinline__ int last_before(const unsigned long long *sorted, uin
 __global__ void __launch_bounds__(1024)
     sample_smem_kernel(RunParams p, uint32_t G, uint32_t k, uint32_t K2,
                        const uint32_t *__restrict__ t, const uint64_t *__restrict__ s,
-                       uint32_t *__restrict__ out_words, uint32_t *__restrict__ out_is) {
+                       uint32_t *__restrict__ out_words, uint32_t *__restrict__ out_is,
+                       const uint32_t *__restrict__ T) {
   extern __shared__ unsigned long long smem[];
   unsigned long long *pairs = smem;                        // K2
   uint32_t *draw = (uint32_t *)(smem + K2);                // k
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(1024)
     const size_t a = (size_t)island * p.n + slot;
     const uint64_t sv = s ? s[a] : 0ull;
     reinterpret_cast<uint4 *>(out_words)[j] =
-        make_uint4(t[a], (uint32_t)sv, (uint32_t)(sv >> 32), G);
+        make_uint4(t[a], (uint32_t)sv, (uint32_t)(sv >> 32), T ? T[a] : G);
     if (out_is) reinterpret_cast<uint2 *>(out_is)[j] = make_uint2(island, slot);
   }
 }
@@ -247,7 +248,7 @@ __global__ void shuffle_serial_kernel(RunParams p, uint32_t G, uint32_t k, uint3
 __global__ void gather_samples_kernel(RunParams p, uint32_t G, uint32_t k, const uint32_t *perm,
                                       const uint32_t *__restrict__ t,
                                       const uint64_t *__restrict__ s, uint32_t *out_words,
-                                      uint32_t *out_is) {
+                                      uint32_t *out_is, const uint32_t *__restrict__ T) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
   const uint32_t island = perm[j];
@@ -255,7 +256,8 @@ __global__ void gather_samples_kernel(RunParams p, uint32_t G, uint32_t k, const
   const uint32_t slot = uindex(w.x, p.n);
   const size_t a = (size_t)island * p.n + slot;
   const uint64_t sv = s ? s[a] : 0ull;
-  reinterpret_cast<uint4 *>(out_words)[j] = make_uint4(t[a], (uint32_t)sv, (uint32_t)(sv >> 32), G);
+  reinterpret_cast<uint4 *>(out_words)[j] =
+      make_uint4(t[a], (uint32_t)sv, (uint32_t)(sv >> 32), T ? T[a] : G);
   if (out_is) reinterpret_cast<uint2 *>(out_is)[j] = make_uint2(island, slot);
 }
 
@@ -265,7 +267,7 @@ size_t sample_scratch_bytes(const RunParams &p, uint32_t k) {
 
 cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint32_t *t,
                           const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
-                          uint32_t *scratch, cudaStream_t stream) {
+                          uint32_t *scratch, cudaStream_t stream, const uint32_t *T) {
   if (k == 0) return cudaSuccess;
   if (k <= kSampleSmemMax) {
     uint32_t K2 = 1;
@@ -274,13 +276,13 @@ cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint
     cudaError_t e = cudaFuncSetAttribute(sample_smem_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sample_smem_kernel<<<1, 1024, smem, stream>>>(p, G, k, K2, t, s, out_words, out_is);
+    sample_smem_kernel<<<1, 1024, smem, stream>>>(p, G, k, K2, t, s, out_words, out_is, T);
     return cudaGetLastError();
   }
   iota_kernel<<<1024, 256, 0, stream>>>(scratch, p.islands);
   shuffle_serial_kernel<<<1, 32, 0, stream>>>(p, G, k, scratch);
   gather_samples_kernel<<<(k + 255) / 256, 256, 0, stream>>>(p, G, k, scratch, t, s, out_words,
-                                                             out_is);
+                                                             out_is, T);
   return cudaGetLastError();
 }
 
