@@ -485,6 +485,40 @@ def run_served(args):
         "dtype": "u32", "data": "synthetic"}), flush=True)
 
 
+def run_async_wafer(args):
+    """Free-running migration on the wafer-shaped grid, advanced in slices of
+    K generations per launch (each island is loaded once and stored once per
+    slice; within a slice islands never wait for one another)."""
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb
+    _build.build()
+    torch.cuda.set_device(0)
+    hb.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    out = []
+    for K in args.slices:
+        with hb.Grid(stream=stream.cuda_stream, mode="async", seed=1, **WORKLOAD) as g:
+            for _ in range(args.warmup):
+                g.run(K)
+            g.sync()
+            steps = max(1, args.async_gens // K)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                g.run(K)
+            e1.record(stream)
+            g.sync()
+            ms = e0.elapsed_time(e1)
+        gens = steps * K
+        out.append({"generations_per_launch": K, "generations": gens,
+                    "value": AGENTS * gens / (ms / 1e3), "us_per_generation": ms * 1e3 / gens})
+    print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
+                      "workload": "wafer-shaped island GA, free-running migration "
+                                  "(512x1024 islands x 32 agents)",
+                      "config": dict(WORKLOAD, mode="async"), "slices": out, "dtype": "u32",
+                      "data": "synthetic"}), flush=True)
+
+
 def run_profile(gens: int):
     """Workload only, for profilers: founders, `gens` generations, one sample."""
     import torch
@@ -510,14 +544,21 @@ def main():
                     help="profiling mode: only run this many generations of the workload "
                          "(no timing); used for ncu captures")
     ap.add_argument("--workload", default="wafer",
-                    choices=["wafer", "tiny", "mid", "batched", "served"],
+                    choices=["wafer", "tiny", "mid", "batched", "served", "async"],
                     help="wafer: the benchmark line; the others: informational lines")
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--memory-cap-mb", type=int, default=2048,
                     help="served workload: device memory cap for admission")
     ap.add_argument("--gen-scale", type=int, default=100,
                     help="batched workload: divide the generation budgets by this")
+    ap.add_argument("--slices", type=int, nargs="+", default=[1, 8, 64, 512],
+                    help="async workload: generations per launch to measure")
+    ap.add_argument("--async-gens", type=int, default=2048,
+                    help="async workload: timed generations per slice length")
     args = ap.parse_args()
+    if args.workload == "async":
+        run_async_wafer(args)
+        return
     if args.workload == "batched":
         run_batched(args)
         return

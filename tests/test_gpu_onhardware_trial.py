@@ -1,0 +1,60 @@
+"""The paper's on-hardware trial ("Results › On-hardware Trial") at its
+array sizes, in integer form, on the GPU: 100x100, 500x500 and 750x750
+islands of 32 agents, tournament size 5, 33% deleterious mutations
+(purifying-only) or the same plus 0.3% beneficial ones (adaption-enabled),
+4 replicates per treatment, one genome sampled per island, reconstruction
+from a 10,000-genome subsample (64-bit tilted surface, 1-bit differentiae).
+The paper's outcome: purifying-only phylogenies have greater sum branch
+length and greater mean evolutionary distinctiveness.  The runs here are
+shorter than the paper's 1,000,000 generations (GENERATIONS below) so the
+test finishes in minutes; reconstruction and phylometrics use the oracle's
+analysis code.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import phylo
+
+pytestmark = pytest.mark.gpu
+
+GENERATIONS = 4000
+SIDES = (100, 500, 750)
+REPLICATES = 4
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_10861_gb300 import _build, binding
+    _build.build()
+    return binding
+
+
+def trial(hb, side, adaptive, seed):
+    kw = dict(rows=side, cols=side, n=32, tournament=5, policy="tilted", bits=1, W=2,
+              p_ben=0.003 if adaptive else 0.0, p_del=0.33, seed=seed)
+    with hb.Grid(**kw) as g:
+        g.run(GENERATIONS)
+        words, _ = g.sample(min(10_000, side * side))
+    surf = words[:, 1].astype(np.uint64) | (words[:, 2].astype(np.uint64) << np.uint64(32))
+    tree = phylo.reconstruct(surf, 1, 1, 2, GENERATIONS)
+    m = phylo.phylometrics(tree)
+    return m["sum_branch_length"], m["mean_evolutionary_distinctiveness"]
+
+
+@pytest.mark.parametrize("side", SIDES)
+def test_purifying_only_has_longer_phylogenies(hb, side):
+    res = {True: [], False: []}
+    for adaptive in (True, False):
+        for r in range(REPLICATES):
+            res[adaptive].append(trial(hb, side, adaptive, seed=7000 + 97 * side + r))
+    adapt = np.array(res[True])
+    purif = np.array(res[False])
+    print(f"side {side}: sum branch length purifying {purif[:, 0].mean():.0f} vs adaptive "
+          f"{adapt[:, 0].mean():.0f}; mean ED {purif[:, 1].mean():.1f} vs {adapt[:, 1].mean():.1f}")
+    for k in (0, 1):
+        assert purif[:, k].min() > adapt[:, k].max()          # every replicate, as in the paper
+        assert stats.mannwhitneyu(purif[:, k], adapt[:, k], alternative="greater").pvalue < 0.05
