@@ -61,15 +61,17 @@ __global__ void __launch_bounds__(512)
     const Deposit dep = deposit_for(p, G);
     const bool do_mig = migrates(p, G);
     if (w.isl0 + kGroup <= p.islands) {
+      PhiloxHead head[AP];
+      replication_heads<AP>(p, G, head);
       if (dep.two)
         full_group<AP, true, false, 0, kInterleave, false, true>(p, dep, G, do_mig, w.isl0, tin,
-                                                                 sin, tout, sout);
+                                                                 sin, tout, sout, head);
       else if (p.tournament == 2)
         full_group<AP, true, true, 0, kInterleave, false>(p, dep, G, do_mig, w.isl0, tin, sin,
-                                                          tout, sout);
+                                                          tout, sout, head);
       else
         full_group<AP, true, false, 0, kInterleave, false>(p, dep, G, do_mig, w.isl0, tin, sin,
-                                                           tout, sout);
+                                                           tout, sout, head);
     } else {
       partial_group<AP, true, false, false>(p, dep, G, do_mig, w.isl0, tin, sin, tout, sout);
     }

@@ -152,6 +152,7 @@ RunParams make_params(const hsga_config *c) {
   p.ben_all = thr_ben >= (1ull << 32) ? 1u : 0u;
   p.bd32 = (uint32_t)thr_bd;
   p.bd_all = thr_bd >= (1ull << 32) ? 1u : 0u;
+  p.has_del = thr_bd > thr_ben ? 1u : 0u;
   p.vmask = (1ull << p.bits) - 1;
   p.cols_div = make_fastdiv(p.cols);
   set_round_keys(p);

@@ -166,6 +166,7 @@ struct RunParams {
   // a5 thresholds floor(p 2^32) in [0, 2^32]: w2 < thr is (w2 < thr32) || thr_all
   uint32_t ben32, ben_all;  // beneficial: w2 < floor(p_ben 2^32)
   uint32_t bd32, bd_all;    // deleterious: otherwise w2 < floor(p_ben 2^32) + floor(p_del 2^32)
+  uint32_t has_del;         // floor(p_del 2^32) > 0
   uint64_t vmask;          // (1 << bits) - 1
   FastDiv cols_div;        // island -> (row, column)
   uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (W0, W1)
@@ -265,6 +266,46 @@ __device__ __forceinline__ uint64_t deposit_into(const Deposit &d, uint64_t s, u
   return ((uint64_t)hi << 32) | lo;
 }
 
+// Philox with counter words 0, 2 and 3 fixed (the child slot per lane, the
+// generation and the purpose per launch): round 1's two products and three
+// of its four outputs do not depend on word 1 (the island), so they are
+// computed once and each island costs one xor plus rounds 2-10.
+struct PhiloxHead {
+  uint32_t x0;   // high(M1 c2) ^ round-1 key 0 (xored with the island later)
+  uint32_t c1;   // low(M1 c2)
+  uint32_t c2;   // high(M0 c0) ^ c3 ^ round-1 key 1
+  uint32_t c3;   // low(M0 c0)
+};
+
+__device__ __forceinline__ PhiloxHead philox_head(uint32_t k0, uint32_t k1, uint32_t c0,
+                                                  uint32_t c2, uint32_t c3) {
+  const uint64_t p0 = (uint64_t)c0 * kPhiloxM0;
+  const uint64_t p1 = (uint64_t)c2 * kPhiloxM1;
+  return PhiloxHead{(uint32_t)(p1 >> 32) ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c3 ^ k1,
+                    (uint32_t)p0};
+}
+
+// Rounds 2-10 after a precomputed head; RK as below.
+template <bool RK>
+__device__ __forceinline__ Words4 philox_tail(const RunParams &p, const PhiloxHead &h,
+                                              uint32_t c1_in) {
+  uint32_t c0 = h.x0 ^ c1_in, c1 = h.c1, c2 = h.c2, c3 = h.c3;
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t k0 = RK ? p.rk0[r] : p.k0 + (uint32_t)r * kPhiloxW0;
+    const uint32_t k1 = RK ? p.rk1[r] : p.k1 + (uint32_t)r * kPhiloxW1;
+    const uint64_t p0 = (uint64_t)c0 * kPhiloxM0;
+    const uint64_t p1 = (uint64_t)c2 * kPhiloxM1;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c0 = n0;
+    c1 = (uint32_t)p1;
+    c2 = n2;
+    c3 = (uint32_t)p0;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
 // RK: the run's round keys are precomputed in the parameter block (single-run
 // kernels); otherwise they are derived from the key in registers.
 template <bool RK>
@@ -290,11 +331,14 @@ __host__ __device__ __forceinline__ bool migrates(const RunParams &p, uint64_t G
 }
 
 // a5: saturating +1 / -1 from the mutation word (thresholds are ordered,
-// floor(p_ben 2^32) <= floor(p_ben 2^32) + floor(p_del 2^32)).
+// floor(p_ben 2^32) <= floor(p_ben 2^32) + floor(p_del 2^32)).  DEL = false:
+// the caller has checked that p_del is 0 (no deleterious branch).
+template <bool DEL = true>
 __device__ __forceinline__ uint32_t mutate(const RunParams &p, uint32_t trait, uint32_t w2) {
   const uint32_t ben = (uint32_t)(w2 < p.ben32) | p.ben_all;
-  const uint32_t bd = (uint32_t)(w2 < p.bd32) | p.bd_all;
   const uint32_t inc = ben & (uint32_t)(trait != 0xFFFFFFFFu);
+  if constexpr (!DEL) return trait + inc;
+  const uint32_t bd = (uint32_t)(w2 < p.bd32) | p.bd_all;
   const uint32_t dec = bd & (ben ^ 1u) & (uint32_t)(trait != 0u);
   return trait + inc - dec;
 }

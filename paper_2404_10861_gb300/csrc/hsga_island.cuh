@@ -38,6 +38,16 @@ __device__ __forceinline__ uint64_t fetch64(const uint64_t (&v)[AP], uint32_t id
   }
 }
 
+// Heads of the replication blocks Philox(seed; j, *, G, 1) of this lane's
+// children j = lane + 32a, for a whole launch at generation G.
+template <int AP>
+__device__ __forceinline__ void replication_heads(const RunParams &p, uint32_t G,
+                                                  PhiloxHead (&h)[AP]) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int a = 0; a < AP; ++a) h[a] = philox_head(p.k0, p.k1, lane + 32u * a, G, kPurposeReplicate);
+}
+
 // Replication words of child j (lane-owned): Philox(seed; j, island, G, 1).
 template <int AP, bool RK = true>
 __device__ __forceinline__ void replication_words(const RunParams &p, uint32_t isl, uint32_t G,
@@ -52,7 +62,8 @@ __device__ __forceinline__ void replication_words(const RunParams &p, uint32_t i
 // runs the same shuffles; children of lanes at or beyond n are garbage and
 // are never stored.  Candidate indices are always < n, so only loaded
 // parents are ever read.  T2: the tournament size is exactly 2.
-template <int AP, bool TRACKED, bool T2 = false, bool RK = true, bool TWO = false>
+template <int AP, bool TRACKED, bool T2 = false, bool RK = true, bool TWO = false,
+          bool DEL = true>
 __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep, uint32_t isl,
                                           uint32_t G, const Words4 (&w)[AP],
                                           const uint32_t (&pt)[AP], const uint64_t (&ps)[AP],
@@ -90,7 +101,7 @@ __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep
       }
     }
     // a5: mutation of the winner's trait.
-    ct[a] = mutate(p, fbest, w[a].z);
+    ct[a] = mutate<DEL>(p, fbest, w[a].z);
     // a6: the child inherits the winner's surface plus one new differentia.
     if constexpr (TRACKED) cs[a] = deposit_into<TWO>(dep, fetch64<AP>(ps, best), w[a].w);
     else cs[a] = 0;
@@ -238,13 +249,14 @@ __device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
 constexpr int kInterleave = 2;
 
 template <int AP, bool TRACKED, bool T2, int NN, int ILV = kInterleave, bool RK = true,
-          bool TWO = false>
+          bool TWO = false, bool DEL = true>
 __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &dep, uint32_t G,
                                            bool do_mig, uint32_t isl0,
                                            const uint32_t *__restrict__ tin,
                                            const uint64_t *__restrict__ sin,
                                            uint32_t *__restrict__ tout,
-                                           uint64_t *__restrict__ sout) {
+                                           uint64_t *__restrict__ sout,
+                                           const PhiloxHead (&head)[AP]) {
   static_assert(kGroup % ILV == 0, "interleave width must divide the group");
   uint32_t pt[kGroup][AP];
   uint64_t ps[kGroup][AP];
@@ -257,7 +269,9 @@ __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &de
   for (uint32_t k = 0; k < kGroup; k += ILV) {
     Words4 w[ILV][AP];
 #pragma unroll
-    for (int i = 0; i < ILV; ++i) replication_words<AP, RK>(p, isl0 + k + i, G, w[i]);
+    for (int i = 0; i < ILV; ++i)
+#pragma unroll
+      for (int a = 0; a < AP; ++a) w[i][a] = philox_tail<RK>(p, head[a], isl0 + k + i);
     if (do_mig) {
 #pragma unroll
       for (int i = 0; i < ILV; ++i) group_land<AP, TRACKED>(gm, k + i, pt[k + i], ps[k + i]);
@@ -266,8 +280,8 @@ __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &de
     uint64_t cs[ILV][AP];
 #pragma unroll
     for (int i = 0; i < ILV; ++i)
-      replicate<AP, TRACKED, T2, RK, TWO>(p, dep, isl0 + k + i, G, w[i], pt[k + i],
-                                          ps[k + i], ct[i], cs[i]);
+      replicate<AP, TRACKED, T2, RK, TWO, DEL>(p, dep, isl0 + k + i, G, w[i], pt[k + i],
+                                               ps[k + i], ct[i], cs[i]);
 #pragma unroll
     for (int i = 0; i < ILV; ++i)
       store_island<AP, TRACKED, NN>(p, isl0 + k + i, tout, sout, ct[i], cs[i]);

@@ -19,21 +19,27 @@ namespace hsga {
 // The group helpers (migration draws, landing plans, island loads/stores)
 // live in hsga_island.cuh.
 template <int AP, bool TRACKED, bool T2, int NN>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, AP == 1 ? kStreamBlocksPerSM : 1)
     step_streamed_kernel(RunParams p, Deposit dep, uint32_t G, int do_mig,
                          const uint32_t *__restrict__ tin, const uint64_t *__restrict__ sin,
                          uint32_t *__restrict__ tout, uint64_t *__restrict__ sout) {
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
   const uint32_t ngroups = (p.islands + kGroup - 1) / kGroup;
+  PhiloxHead head[AP];
+  replication_heads<AP>(p, G, head);
   for (uint32_t grp = blockIdx.x * wpb + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
     const uint32_t isl0 = grp * kGroup;
     if (isl0 + kGroup <= p.islands) {
       if (dep.two)
         full_group<AP, TRACKED, T2, NN, kInterleave, true, true>(p, dep, G, do_mig != 0, isl0,
-                                                                 tin, sin, tout, sout);
+                                                                 tin, sin, tout, sout, head);
+      else if (p.has_del)
+        full_group<AP, TRACKED, T2, NN>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout,
+                                        head);
       else
-        full_group<AP, TRACKED, T2, NN>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
+        full_group<AP, TRACKED, T2, NN, kInterleave, true, false, false>(
+            p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout, head);
     }
     else
       partial_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
