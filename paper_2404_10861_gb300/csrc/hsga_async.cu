@@ -2,8 +2,8 @@
 //
 // The paper's islands run without a global clock, each taking whatever its
 // neighbours last sent (section "Asynchronous Island-model Genetic
-// Algorithm").  Here one warp owns one island (lane = agent, n <= 32) and
-// runs its generations without ever waiting: at every migrating generation
+// Algorithm").  Here a warp owns a few islands (lane = agent, n <= 32) and
+// runs their generations without ever waiting: at every migrating generation
 // it publishes its emigrant (slot and direction from the counter-based RNG,
 // as in synchronous mode) into its single outgoing record, then looks at
 // each neighbour's latest record and takes it if that record is new and was
@@ -52,143 +52,190 @@ __device__ __forceinline__ void fence_acq_rel() {
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
-template <bool TRACKED, bool T2, bool TWO>
+// IPW islands per warp share the fences of a generation: the writer lanes
+// (one per island) fence once before their records, and the reader lanes (one
+// per island and direction) fence once between the records and the
+// re-checked stamps.
+template <bool TRACKED, bool T2, bool TWO, int IPW>
 __global__ void __launch_bounds__(kResidentThreads)
     step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                       uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
                       uint4 *__restrict__ rec, uint32_t *__restrict__ stamp,
                       uint32_t *__restrict__ seen_io, uint32_t *__restrict__ log,
                       uint32_t log_G0, uint32_t log_gens) {
+  static_assert(4 * IPW <= 32, "one reader lane per island and direction");
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t isl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (isl >= p.islands) return;  // whole warps only; no block barriers are used
+  const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint32_t first = warp * IPW;
+  if (first >= p.islands) return;  // whole warps only; no block barriers are used
   const uint32_t n = p.n;
-  const uint32_t base = isl * n;
-  uint32_t pt[1] = {0}, pT[1] = {0};
-  uint64_t ps[1] = {0};
-  if (lane < n) {
-    pt[0] = tplane[base + lane];
-    if constexpr (TRACKED) ps[0] = splane[base + lane];
-    pT[0] = Tplane[base + lane];
+  uint32_t isl[IPW];
+  bool live[IPW];
+  uint32_t pt[IPW][1], pT[IPW][1];
+  uint64_t ps[IPW][1];
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    isl[k] = first + k;
+    live[k] = isl[k] < p.islands;
+    pt[k][0] = pT[k][0] = 0;
+    ps[k][0] = 0;
+    if (live[k] && lane < n) {
+      pt[k][0] = tplane[isl[k] * n + lane];
+      if constexpr (TRACKED) ps[k][0] = splane[isl[k] * n + lane];
+      pT[k][0] = Tplane[isl[k] * n + lane];
+    }
   }
-  uint32_t seen = lane < 4 ? seen_io[isl * 4 + lane] : 0u;
+  // reader lane r = 4k + d: island k, direction d
+  const uint32_t rk = lane >> 2, rd = lane & 3u;
+  const bool reader = lane < 4u * IPW && first + rk < p.islands;
+  const uint32_t risl = first + rk;
+  uint32_t seen = reader ? seen_io[risl * 4 + rd] : 0u;
+  const uint32_t rnb = reader ? neighbour(p, risl, rd) : 0u;
+  // block lane b: b < IPW the emigrant block of island b, IPW <= b < 2 IPW
+  // the placement block of island b - IPW
+  const uint32_t bk = lane < (uint32_t)IPW ? lane : (lane < 2u * IPW ? lane - IPW : 0u);
   for (uint32_t g = 0; g < ngen; ++g) {
     const uint32_t G = G0 + g;
-    Words4 w[1];
-    replication_words<1>(p, isl, G, w);
     const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
     if (migrates(p, G)) {
-      // lane 0: the emigrant block, lane 1: the placement block
-      const Words4 m =
-          philox_rk(p, lane == 1 ? kSlotImmigrant : kSlotEmigrant, isl, G, kPurposeMigration);
-      const uint32_t eslot = uindex(__shfl_sync(kFull, m.x, 0), n);
-      const uint32_t dir = __shfl_sync(kFull, m.y, 0) >> 30;
-      const uint32_t te = __shfl_sync(kFull, pt[0], eslot);
-      const uint64_t se = shfl64(ps[0], eslot);
-      const uint32_t Te = __shfl_sync(kFull, pT[0], eslot);
-      // a1: publish under the stamp
-      if (lane == 0) {
-        st_relaxed_u32(stamp + isl, ((G + 1u) << 3) | 1u);
-        fence_acq_rel();
-        rec[isl] = make_uint4(te, (uint32_t)se, (uint32_t)(se >> 32), Te);
-        st_release_u32(stamp + isl, ((G + 1u) << 3) | (dir << 1));
+      const Words4 m = philox_rk(p, lane >= (uint32_t)IPW ? kSlotImmigrant : kSlotEmigrant,
+                                 first + bk, G, kPurposeMigration);
+      // a1: lane k gathers island k's emigrant
+      uint32_t te = 0, Te = 0, dir = 0;
+      uint64_t se = 0;
+#pragma unroll
+      for (int k = 0; k < IPW; ++k) {
+        const uint32_t eslot = uindex(__shfl_sync(kFull, m.x, k), n);
+        const uint32_t dk = __shfl_sync(kFull, m.y, k) >> 30;
+        const uint32_t vt = __shfl_sync(kFull, pt[k][0], eslot);
+        const uint64_t vs = shfl64(ps[k][0], eslot);
+        const uint32_t vT = __shfl_sync(kFull, pT[k][0], eslot);
+        if (lane == (uint32_t)k) {
+          te = vt;
+          se = vs;
+          Te = vT;
+          dir = dk;
+        }
       }
-      // a2: each neighbour's latest record, if new and aimed here
-      bool take = false;
-      uint32_t it = 0, iT = 0, from = 0;
-      uint64_t is = 0;
-      if (lane < 4) {
-        const uint32_t nb = neighbour(p, isl, lane);
-        const uint32_t s1 = ld_acquire_u32(stamp + nb);
+      const bool writer = lane < (uint32_t)IPW && first + lane < p.islands;
+      if (writer) st_relaxed_u32(stamp + first + lane, ((G + 1u) << 3) | 1u);
+      fence_acq_rel();
+      if (writer) {
+        rec[first + lane] = make_uint4(te, (uint32_t)se, (uint32_t)(se >> 32), Te);
+        st_release_u32(stamp + first + lane, ((G + 1u) << 3) | (dir << 1));
+      }
+      // a2: each reader lane looks at its neighbour's latest record
+      uint32_t s1 = 0;
+      bool cand = false;
+      uint4 r = make_uint4(0, 0, 0, 0);
+      if (reader) {
+        s1 = ld_acquire_u32(stamp + rnb);
         if (!(s1 & 1u) && (s1 >> 3) > seen) {
           seen = s1 >> 3;
-          if (((s1 >> 1) & 3u) == ((lane + 2u) & 3u)) {
-            const uint4 r = __ldcg(rec + nb);
-            fence_acq_rel();
-            if (ld_relaxed_u32(stamp + nb) == s1) {
-              take = true;
-              it = r.x;
-              is = ((uint64_t)r.z << 32) | r.y;
-              iT = r.w;
-              from = s1 >> 3;
-            }
+          if (((s1 >> 1) & 3u) == ((rd + 2u) & 3u)) {
+            cand = true;
+            r = __ldcg(rec + rnb);
           }
         }
-        if (logging) log[((size_t)isl * log_gens + (G - log_G0)) * 4 + lane] = from;
       }
+      fence_acq_rel();
+      bool take = false;
+      if (cand) take = ld_relaxed_u32(stamp + rnb) == s1;
+      if (reader && logging)
+        log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = take ? (s1 >> 3) : 0u;
+      const uint32_t it = r.x, iT = r.w;
+      const uint64_t is = ((uint64_t)r.z << 32) | r.y;
       const uint32_t arrivals = __ballot_sync(kFull, take);
       const uint32_t place[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
-      for (uint32_t dd = 0; dd < 4; ++dd) {
-        if (arrivals & (1u << dd)) {
-          const uint32_t slot = uindex(__shfl_sync(kFull, place[dd], 1), n);
-          const uint32_t vt = __shfl_sync(kFull, it, dd);
-          const uint64_t vs = shfl64(is, dd);
-          const uint32_t vT = __shfl_sync(kFull, iT, dd);
-          if (lane == slot) {
-            pt[0] = vt;
-            ps[0] = vs;
-            pT[0] = vT;
-          }
-        }
-      }
-    } else if (logging && lane < 4) {
-      log[((size_t)isl * log_gens + (G - log_G0)) * 4 + lane] = 0;
-    }
-    // a3-a5: tournament and mutation on the traits
-    uint32_t best = uindex(w[0].x, n);
-    uint32_t fbest = fetch32<1>(pt, best);
-    if (T2 || p.tournament >= 2) {
-      const uint32_t c = uindex(w[0].y, n);
-      const uint32_t fc = fetch32<1>(pt, c);
-      const bool pick = fc > fbest;
-      best = pick ? c : best;
-      fbest = pick ? fc : fbest;
-    }
-    if constexpr (!T2) {
-      for (uint32_t c0 = 2; c0 < p.tournament; c0 += 4) {
-        const Words4 e = philox_rk(p, lane, isl, G, kPurposeReplicate + 1 + (c0 - 2) / 4);
-        const uint32_t ew[4] = {e.x, e.y, e.z, e.w};
+      for (int k = 0; k < IPW; ++k) {
+        const uint32_t bits = (arrivals >> (4 * k)) & 0xFu;
+        if (!bits) continue;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (c0 + r < p.tournament) {
-            const uint32_t c = uindex(ew[r], n);
-            const uint32_t fc = fetch32<1>(pt, c);
-            if (fc > fbest) {
-              best = c;
-              fbest = fc;
+        for (uint32_t dd = 0; dd < 4; ++dd) {
+          if (bits & (1u << dd)) {
+            const uint32_t slot = uindex(__shfl_sync(kFull, place[dd], IPW + k), n);
+            const uint32_t src = 4u * k + dd;
+            const uint32_t vt = __shfl_sync(kFull, it, src);
+            const uint64_t vs = shfl64(is, src);
+            const uint32_t vT = __shfl_sync(kFull, iT, src);
+            if (lane == slot) {
+              pt[k][0] = vt;
+              ps[k][0] = vs;
+              pT[k][0] = vT;
             }
           }
         }
       }
+    } else if (reader && logging) {
+      log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = 0;
     }
-    const uint32_t child_t = mutate(p, fbest, w[0].z);
-    // a6: deposit at the site of the parent's own counter
-    const uint32_t Tp = fetch32<1>(pT, best);
-    uint64_t child_s = 0;
-    if constexpr (TRACKED) {
-      const Deposit dep = deposit_unpack(deposit_pack(p, Tp), (uint32_t)p.vmask);
-      child_s = deposit_into<TWO>(dep, fetch64<1>(ps, best), w[0].w);
+    // a3-a6 for every owned island, with per-genome counters
+#pragma unroll
+    for (int k = 0; k < IPW; ++k) {
+      if (!live[k]) continue;
+      const Words4 w = philox_rk(p, lane, isl[k], G, kPurposeReplicate);
+      uint32_t best = uindex(w.x, n);
+      uint32_t fbest = fetch32<1>(pt[k], best);
+      if (T2 || p.tournament >= 2) {
+        const uint32_t c = uindex(w.y, n);
+        const uint32_t fc = fetch32<1>(pt[k], c);
+        const bool pick = fc > fbest;
+        best = pick ? c : best;
+        fbest = pick ? fc : fbest;
+      }
+      if constexpr (!T2) {
+        for (uint32_t c0 = 2; c0 < p.tournament; c0 += 4) {
+          const Words4 e = philox_rk(p, lane, isl[k], G, kPurposeReplicate + 1 + (c0 - 2) / 4);
+          const uint32_t ew[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (c0 + q < p.tournament) {
+              const uint32_t c = uindex(ew[q], n);
+              const uint32_t fc = fetch32<1>(pt[k], c);
+              if (fc > fbest) {
+                best = c;
+                fbest = fc;
+              }
+            }
+          }
+        }
+      }
+      const uint32_t child_t = mutate(p, fbest, w.z);
+      const uint32_t Tp = fetch32<1>(pT[k], best);
+      uint64_t child_s = 0;
+      if constexpr (TRACKED) {
+        const Deposit dep = deposit_unpack(deposit_pack(p, Tp), (uint32_t)p.vmask);
+        child_s = deposit_into<TWO>(dep, fetch64<1>(ps[k], best), w.w);
+      }
+      pt[k][0] = child_t;
+      ps[k][0] = child_s;
+      pT[k][0] = Tp + 1u;
     }
-    pt[0] = child_t;
-    ps[0] = child_s;
-    pT[0] = Tp + 1u;
   }
-  if (lane < n) {
-    tplane[base + lane] = pt[0];
-    if constexpr (TRACKED) splane[base + lane] = ps[0];
-    Tplane[base + lane] = pT[0];
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    if (live[k] && lane < n) {
+      tplane[isl[k] * n + lane] = pt[k][0];
+      if constexpr (TRACKED) splane[isl[k] * n + lane] = ps[k][0];
+      Tplane[isl[k] * n + lane] = pT[k][0];
+    }
   }
-  if (lane < 4) seen_io[isl * 4 + lane] = seen;
+  if (reader) seen_io[risl * 4 + rd] = seen;
 }
+
+constexpr int kAsyncIslandsPerWarp = 4;
 
 using AsyncFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
                          uint4 *, uint32_t *, uint32_t *, uint32_t *, uint32_t, uint32_t);
 
 AsyncFn pick_async(bool tracked, bool t2, bool two) {
-  if (!tracked) return t2 ? step_async_kernel<false, true, false> : step_async_kernel<false, false, false>;
-  if (two) return t2 ? step_async_kernel<true, true, true> : step_async_kernel<true, false, true>;
-  return t2 ? step_async_kernel<true, true, false> : step_async_kernel<true, false, false>;
+  constexpr int I = kAsyncIslandsPerWarp;
+  if (!tracked)
+    return t2 ? step_async_kernel<false, true, false, I> : step_async_kernel<false, false, false, I>;
+  if (two)
+    return t2 ? step_async_kernel<true, true, true, I> : step_async_kernel<true, false, true, I>;
+  return t2 ? step_async_kernel<true, true, false, I> : step_async_kernel<true, false, false, I>;
 }
 
 }  // namespace
@@ -199,7 +246,8 @@ cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, ui
                               cudaStream_t stream) {
   AsyncFn fn = pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID);
   const uint32_t wpb = kResidentThreads / 32;
-  const uint32_t blocks = (p.islands + wpb - 1) / wpb;
+  const uint32_t warps = (p.islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
+  const uint32_t blocks = (warps + wpb - 1) / wpb;
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, rec, stamp, seen, log,
                                                log_G0, log_gens);
   return cudaGetLastError();
