@@ -4,16 +4,19 @@
 // neighbours last sent (section "Asynchronous Island-model Genetic
 // Algorithm").  Here a warp owns a few islands (lane = agent, n <= 32) and
 // runs their generations without ever waiting: at every migrating generation
-// it publishes its emigrant (slot and direction from the counter-based RNG,
-// as in synchronous mode) into its single outgoing record, then looks at
-// each neighbour's latest record and takes it if that record is new and was
-// aimed at this island.  Records are guarded by a sequence stamp (a
-// seqlock): the writer marks the stamp odd, writes the 16-byte genome, then
-// publishes an even stamp ((G+1) << 3 | dir << 1) with a release store; a
-// reader accepts the genome only if the stamp it acquired before reading is
-// even, newer than the last one it saw from that neighbour, and unchanged
-// after the read.  A record overwritten before a neighbour saw it is simply
-// lost (the paper's dropped messages).  Genomes carry their own deposition
+// it publishes each island's emigrant (slot and direction from the
+// counter-based RNG, as in synchronous mode) into that island's single
+// outgoing record, then looks at each neighbour's latest record and takes it
+// if that record is new and was aimed at this island.  A record is four
+// 64-bit words, each holding one 32-bit word of the genome (trait, surface
+// low, surface high, counter T) under the same 32-bit stamp
+// ((G+1) << 3 | dir << 1).  A 64-bit relaxed access is single-copy atomic,
+// so a reader that sees one stamp in all four words holds one whole record
+// (exactly one record carries each stamp); a reader that sees mixed stamps
+// caught a record being rewritten and ignores it.  No fence is needed on
+// either side.  A record is taken if its stamp is newer than the last one
+// the reader saw from that neighbour; a record overwritten before a
+// neighbour saw it is simply lost (the paper's dropped messages).  Genomes carry their own deposition
 // counter T: an immigrant keeps its T, a child deposits at site(T_parent)
 // and carries T_parent + 1.
 //
@@ -28,42 +31,25 @@
 namespace hsga {
 namespace {
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void fence_acq_rel() {
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");
-}
-
-// IPW islands per warp share the fences of a generation: the writer lanes
-// (one per island) fence once before their records, and the reader lanes (one
-// per island and direction) fence once between the records and the
-// re-checked stamps.
+// IPW islands per warp: lane 4k + j writes word j of island k's record, and
+// lane 4k + d reads the record of island k's neighbour in direction d.
 template <bool TRACKED, bool T2, bool TWO, int IPW>
 __global__ void __launch_bounds__(kResidentThreads)
     step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                       uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
-                      uint4 *__restrict__ rec, uint32_t *__restrict__ stamp,
-                      uint32_t *__restrict__ seen_io, uint32_t *__restrict__ log,
+                      uint64_t *__restrict__ rec, uint32_t *__restrict__ seen_io, uint32_t *__restrict__ log,
                       uint32_t log_G0, uint32_t log_gens) {
-  static_assert(4 * IPW <= 32, "one reader lane per island and direction");
+  static_assert(4 * IPW <= 32, "one lane per island and record word or direction");
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const uint32_t first = warp * IPW;
@@ -100,9 +86,8 @@ __global__ void __launch_bounds__(kResidentThreads)
     if (migrates(p, G)) {
       const Words4 m = philox_rk(p, lane >= (uint32_t)IPW ? kSlotImmigrant : kSlotEmigrant,
                                  first + bk, G, kPurposeMigration);
-      // a1: lane k gathers island k's emigrant
-      uint32_t te = 0, Te = 0, dir = 0;
-      uint64_t se = 0;
+      // a1: lane 4k + j gathers word j of island k's emigrant and publishes it
+      uint32_t word = 0, dir = 0;
 #pragma unroll
       for (int k = 0; k < IPW; ++k) {
         const uint32_t eslot = uindex(__shfl_sync(kFull, m.x, k), n);
@@ -110,41 +95,36 @@ __global__ void __launch_bounds__(kResidentThreads)
         const uint32_t vt = __shfl_sync(kFull, pt[k][0], eslot);
         const uint64_t vs = shfl64(ps[k][0], eslot);
         const uint32_t vT = __shfl_sync(kFull, pT[k][0], eslot);
-        if (lane == (uint32_t)k) {
-          te = vt;
-          se = vs;
-          Te = vT;
+        if (rk == (uint32_t)k) {
+          word = rd == 0 ? vt : rd == 1 ? (uint32_t)vs : rd == 2 ? (uint32_t)(vs >> 32) : vT;
           dir = dk;
         }
       }
-      const bool writer = lane < (uint32_t)IPW && first + lane < p.islands;
-      if (writer) st_relaxed_u32(stamp + first + lane, ((G + 1u) << 3) | 1u);
-      fence_acq_rel();
-      if (writer) {
-        rec[first + lane] = make_uint4(te, (uint32_t)se, (uint32_t)(se >> 32), Te);
-        st_release_u32(stamp + first + lane, ((G + 1u) << 3) | (dir << 1));
+      if (reader) {
+        const uint32_t st = ((G + 1u) << 3) | (dir << 1);
+        st_relaxed_u64(rec + 4 * (size_t)risl + rd, ((uint64_t)st << 32) | word);
       }
       // a2: each reader lane looks at its neighbour's latest record
-      uint32_t s1 = 0;
-      bool cand = false;
-      uint4 r = make_uint4(0, 0, 0, 0);
-      if (reader) {
-        s1 = ld_acquire_u32(stamp + rnb);
-        if (!(s1 & 1u) && (s1 >> 3) > seen) {
-          seen = s1 >> 3;
-          if (((s1 >> 1) & 3u) == ((rd + 2u) & 3u)) {
-            cand = true;
-            r = __ldcg(rec + rnb);
-          }
-        }
-      }
-      fence_acq_rel();
       bool take = false;
-      if (cand) take = ld_relaxed_u32(stamp + rnb) == s1;
+      uint32_t s1 = 0, r[4] = {0, 0, 0, 0};
+      if (reader) {
+        uint64_t v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = ld_relaxed_u64(rec + 4 * (size_t)rnb + j);
+        s1 = (uint32_t)(v[0] >> 32);
+        const bool whole = (uint32_t)(v[1] >> 32) == s1 && (uint32_t)(v[2] >> 32) == s1 &&
+                           (uint32_t)(v[3] >> 32) == s1;
+        if (whole && (s1 >> 3) > seen) {
+          seen = s1 >> 3;
+          take = ((s1 >> 1) & 3u) == ((rd + 2u) & 3u);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = (uint32_t)v[j];
+      }
       if (reader && logging)
         log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = take ? (s1 >> 3) : 0u;
-      const uint32_t it = r.x, iT = r.w;
-      const uint64_t is = ((uint64_t)r.z << 32) | r.y;
+      const uint32_t it = r[0], iT = r[3];
+      const uint64_t is = ((uint64_t)r[2] << 32) | r[1];
       const uint32_t arrivals = __ballot_sync(kFull, take);
       const uint32_t place[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
@@ -224,10 +204,10 @@ __global__ void __launch_bounds__(kResidentThreads)
   if (reader) seen_io[risl * 4 + rd] = seen;
 }
 
-constexpr int kAsyncIslandsPerWarp = 4;
+constexpr int kAsyncIslandsPerWarp = 8;
 
 using AsyncFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
-                         uint4 *, uint32_t *, uint32_t *, uint32_t *, uint32_t, uint32_t);
+                         uint64_t *, uint32_t *, uint32_t *, uint32_t, uint32_t);
 
 AsyncFn pick_async(bool tracked, bool t2, bool two) {
   constexpr int I = kAsyncIslandsPerWarp;
@@ -241,15 +221,15 @@ AsyncFn pick_async(bool tracked, bool t2, bool two) {
 }  // namespace
 
 cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t *t,
-                              uint64_t *s, uint32_t *T, uint4 *rec, uint32_t *stamp,
-                              uint32_t *seen, uint32_t *log, uint32_t log_G0, uint32_t log_gens,
+                              uint64_t *s, uint32_t *T, uint64_t *rec, uint32_t *seen,
+                              uint32_t *log, uint32_t log_G0, uint32_t log_gens,
                               cudaStream_t stream) {
   AsyncFn fn = pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID);
   const uint32_t wpb = kResidentThreads / 32;
   const uint32_t warps = (p.islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
   const uint32_t blocks = (warps + wpb - 1) / wpb;
-  fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, rec, stamp, seen, log,
-                                               log_G0, log_gens);
+  fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, rec, seen, log, log_G0,
+                                               log_gens);
   return cudaGetLastError();
 }
 

@@ -214,6 +214,8 @@ cudaError_t fill_u32(uint32_t *dst, uint32_t value, uint64_t count, cudaStream_t
 
 int reset_sync_state(hsga_grid *g) {
   cudaError_t e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+  if (e == cudaSuccess && g->async)
+    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess && g->seen)
     e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), g->stream);
@@ -415,7 +417,7 @@ int advance(hsga_grid *g, uint64_t n) {
     for (uint64_t done = 0; done < n && e == cudaSuccess;) {
       const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
       e = launch_step_async(g->p, (uint32_t)(g->G + done), m, g->trait[g->cur], g->surf[g->cur],
-                            g->tcount, g->rec, g->flags, g->seen, g->alog,
+                            g->tcount, reinterpret_cast<uint64_t *>(g->rec), g->seen, g->alog,
                             (uint32_t)g->alog_G0, g->alog_gens, g->stream);
       g->launches++;
       done += m;
@@ -522,7 +524,7 @@ int hsga_set_async_log(hsga_grid *g, uint32_t generations) {
   cudaError_t e = cudaMemsetAsync(g->alog, 0, bytes, g->stream);
   // a fresh window: nothing published before it can be taken
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
   g->alog_gens = generations;
