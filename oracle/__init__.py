@@ -125,6 +125,11 @@ def lib():
         _lib.orc_sample_grid.restype = ctypes.c_int
         _lib.orc_run_async.argtypes = [P(_Cfg), P(u32), P(u64), P(u32), u64, u32, P(u32)]
         _lib.orc_run_async.restype = ctypes.c_int
+        _lib.orc_island_step.argtypes = [P(_Cfg), u32, u64, P(u32), P(u64), P(u32)]
+        _lib.orc_island_step.restype = ctypes.c_int
+        _lib.orc_run_buffered.argtypes = [P(_Cfg), P(u32), P(u64), P(u32), u64, u32, P(u32),
+                                          P(u32), P(u32)]
+        _lib.orc_run_buffered.restype = ctypes.c_int
     return _lib
 
 
@@ -266,6 +271,47 @@ def run_async(cfg: Config, trait, surf, tcount, G0: int, generations: int, sched
     if rc != 0:
         raise MemoryError("oracle async run failed")
     return trait, surf, tcount
+
+
+def island_step(cfg: Config, island: int, G: int, trait, surf, tcount) -> None:
+    """One generation (a3-a6) of one island with per-genome deposition
+    counters, in place on the whole-grid arrays (uint32, uint64, uint32,
+    C-contiguous)."""
+    for a, t in ((trait, np.uint32), (surf, np.uint64), (tcount, np.uint32)):
+        if a.dtype != t or not a.flags.c_contiguous:
+            raise TypeError("island_step works in place on contiguous arrays")
+    c = cfg._c()
+    if lib().orc_island_step(ctypes.byref(c), island, G, _p(trait, ctypes.c_uint32),
+                             _p(surf, ctypes.c_uint64), _p(tcount, ctypes.c_uint32)):
+        raise MemoryError("oracle island step failed")
+
+
+def run_buffered(cfg: Config, trait, surf, tcount, G0: int, generations: int, log):
+    """Buffered free-running migration (per-neighbour emigration buffers of
+    one genome, immigration buffers of four) replayed from a log (see
+    hsga_oracle.c): log[island, g, d] = (post number taken from direction d)
+    << 1 | (1 if the island posted toward d).  Returns (trait, surf, tcount,
+    chan, inbuf): chan[island, d] = (posts made toward d, last post number
+    taken from d, genomes waiting), inbuf[island, d, j] = (trait, surface lo,
+    surface hi, T) of waiting genome j."""
+    trait = np.ascontiguousarray(trait, dtype=np.uint32).copy()
+    surf = np.ascontiguousarray(surf, dtype=np.uint64).copy()
+    tcount = np.ascontiguousarray(tcount, dtype=np.uint32).copy()
+    lg = np.ascontiguousarray(log, dtype=np.uint32).reshape(-1)
+    if lg.size != cfg.islands * generations * 4:
+        raise ValueError("log must be islands x generations x 4")
+    chan = np.zeros((cfg.islands, 4, 3), dtype=np.uint32)
+    inbuf = np.zeros((cfg.islands, 4, 4, 4), dtype=np.uint32)
+    c = cfg._c()
+    rc = lib().orc_run_buffered(ctypes.byref(c), _p(trait, ctypes.c_uint32),
+                                _p(surf, ctypes.c_uint64), _p(tcount, ctypes.c_uint32), G0,
+                                generations, _p(lg, ctypes.c_uint32),
+                                _p(chan, ctypes.c_uint32), _p(inbuf, ctypes.c_uint32))
+    if rc == -3:
+        raise ValueError("log breaks the buffered protocol or its causality")
+    if rc != 0:
+        raise MemoryError("oracle buffered run failed")
+    return trait, surf, tcount, chan, inbuf
 
 
 def sync_schedule(cfg: Config, G0: int, generations: int) -> np.ndarray:

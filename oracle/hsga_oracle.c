@@ -526,6 +526,76 @@ int orc_sample_grid(const orc_cfg *cfg, const uint32_t *trait,
 }
 
 /* ------------------------------------------------------------------ */
+/* One generation (a3-a6) of island i when genomes carry their own
+ * deposition counters (free-running modes): each child deposits at
+ * site_fn(T_parent) and carries T_parent + 1 (the paper's per-genome
+ * generation counter, "Methods › Genome Model"); the Philox draws are those
+ * of the synchronous step.  Updates island i of trait, surf and tcount in
+ * place.  Returns 0 or -1 on allocation failure. */
+int orc_island_step(const orc_cfg *cfg, uint32_t i, uint64_t G, uint32_t *trait,
+                    uint64_t *surf, uint32_t *tcount) {
+  uint32_t n = cfg->n;
+  uint32_t S = 64 / cfg->bits;
+  uint64_t vmask = (1ull << cfg->bits) - 1;
+  uint64_t thr_b = orc_threshold(cfg->p_ben), thr_d = orc_threshold(cfg->p_del);
+  uint32_t *ct = malloc(sizeof(uint32_t) * n), *cT = malloc(sizeof(uint32_t) * n);
+  uint64_t *cs = malloc(sizeof(uint64_t) * n);
+  if (!ct || !cT || !cs) {
+    free(ct); free(cT); free(cs);
+    return -1;
+  }
+  const uint32_t *fit = trait + (size_t)i * n;
+  for (uint32_t j = 0; j < n; ++j) {
+    uint32_t w[4];
+    orc_draw(cfg->seed, j, i, (uint32_t)G, 1, w);
+    uint32_t best = orc_index(w[0], n);
+    for (uint32_t c = 1; c < cfg->tournament; ++c) {
+      uint32_t word;
+      if (c == 1) {
+        word = w[1];
+      } else {
+        uint32_t extra[4];
+        orc_draw(cfg->seed, j, i, (uint32_t)G, 2 + (c - 2) / 4, extra);
+        word = extra[(c - 2) % 4];
+      }
+      uint32_t cand = orc_index(word, n);
+      if (fit[cand] > fit[best]) best = cand;
+    }
+    size_t pa = (size_t)i * n + best;
+    uint32_t tr = trait[pa];
+    uint64_t su = surf[pa];
+    uint32_t T = tcount[pa];
+    if ((uint64_t)w[2] < thr_b) {
+      if (tr != 0xFFFFFFFFu) tr += 1;
+    } else if ((uint64_t)w[2] < thr_b + thr_d) {
+      if (tr != 0) tr -= 1;
+    }
+    if (cfg->policy != ORC_NONE) {
+      uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
+      if (site < S) {
+        su &= ~(vmask << (site * cfg->bits));
+        su |= ((uint64_t)w[3] & vmask) << (site * cfg->bits);
+      }
+      if (cfg->policy == ORC_HYBRID) {
+        uint32_t site2 = orc_hybrid_second_site(S, cfg->W, T);
+        if (site2 < S) {
+          su &= ~(vmask << (site2 * cfg->bits));
+          su |= ((uint64_t)(w[3] >> 16) & vmask) << (site2 * cfg->bits);
+        }
+      }
+    }
+    ct[j] = tr;
+    cs[j] = su;
+    cT[j] = T + 1;
+  }
+  memcpy(trait + (size_t)i * n, ct, sizeof(uint32_t) * n);
+  memcpy(surf + (size_t)i * n, cs, sizeof(uint64_t) * n);
+  memcpy(tcount + (size_t)i * n, cT, sizeof(uint32_t) * n);
+  free(ct); free(cT); free(cs);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Free-running (asynchronous) migration, replayed from a schedule.
  *
  * The paper's WSE islands run without a global clock: each keeps one
@@ -550,16 +620,11 @@ int orc_run_async(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
                   uint32_t *tcount, uint64_t G0, uint32_t n_gens,
                   const uint32_t *sched) {
   uint32_t I = cfg->rows * cfg->cols, n = cfg->n;
-  uint32_t S = 64 / cfg->bits;
-  uint64_t vmask = (1ull << cfg->bits) - 1;
-  uint64_t thr_b = orc_threshold(cfg->p_ben), thr_d = orc_threshold(cfg->p_del);
   /* emigrant records by island and generation: trait, lo, hi, T, dir */
   uint32_t *hist = malloc(sizeof(uint32_t) * 5 * (size_t)I * (n_gens + 1));
   uint32_t *done = calloc(I, sizeof(uint32_t));
-  uint32_t *ct = malloc(sizeof(uint32_t) * n), *cT = malloc(sizeof(uint32_t) * n);
-  uint64_t *cs = malloc(sizeof(uint64_t) * n);
-  if (!hist || !done || !ct || !cT || !cs) {
-    free(hist); free(done); free(ct); free(cT); free(cs);
+  if (!hist || !done) {
+    free(hist); free(done);
     return -1;
   }
   /* the emigrant each island publishes at the start of its generation g */
@@ -612,53 +677,7 @@ int orc_run_async(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
       }
       if (status) break;
       /* a3-a6 with per-genome counters */
-      const uint32_t *fit = trait + (size_t)i * n;
-      for (uint32_t j = 0; j < n; ++j) {
-        uint32_t w[4];
-        orc_draw(cfg->seed, j, i, (uint32_t)G, 1, w);
-        uint32_t best = orc_index(w[0], n);
-        for (uint32_t c = 1; c < cfg->tournament; ++c) {
-          uint32_t word;
-          if (c == 1) {
-            word = w[1];
-          } else {
-            uint32_t extra[4];
-            orc_draw(cfg->seed, j, i, (uint32_t)G, 2 + (c - 2) / 4, extra);
-            word = extra[(c - 2) % 4];
-          }
-          uint32_t cand = orc_index(word, n);
-          if (fit[cand] > fit[best]) best = cand;
-        }
-        size_t pa = (size_t)i * n + best;
-        uint32_t tr = trait[pa];
-        uint64_t su = surf[pa];
-        uint32_t T = tcount[pa];
-        if ((uint64_t)w[2] < thr_b) {
-          if (tr != 0xFFFFFFFFu) tr += 1;
-        } else if ((uint64_t)w[2] < thr_b + thr_d) {
-          if (tr != 0) tr -= 1;
-        }
-        if (cfg->policy != ORC_NONE) {
-          uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
-          if (site < S) {
-            su &= ~(vmask << (site * cfg->bits));
-            su |= ((uint64_t)w[3] & vmask) << (site * cfg->bits);
-          }
-          if (cfg->policy == ORC_HYBRID) {
-            uint32_t site2 = orc_hybrid_second_site(S, cfg->W, T);
-            if (site2 < S) {
-              su &= ~(vmask << (site2 * cfg->bits));
-              su |= ((uint64_t)(w[3] >> 16) & vmask) << (site2 * cfg->bits);
-            }
-          }
-        }
-        ct[j] = tr;
-        cs[j] = su;
-        cT[j] = T + 1;
-      }
-      memcpy(trait + (size_t)i * n, ct, sizeof(uint32_t) * n);
-      memcpy(surf + (size_t)i * n, cs, sizeof(uint64_t) * n);
-      memcpy(tcount + (size_t)i * n, cT, sizeof(uint32_t) * n);
+      if (orc_island_step(cfg, i, G, trait, surf, tcount)) { status = -1; break; }
       done[i] = g + 1;
       ORC_PUBLISH(i, g + 1);
       --remaining;
@@ -667,6 +686,161 @@ int orc_run_async(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
     if (!progress && status == 0) status = -3;
   }
 #undef ORC_PUBLISH
-  free(hist); free(done); free(ct); free(cT); free(cs);
+  free(hist); free(done);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Buffered free-running migration (the WSE's per-neighbour buffers),
+ * replayed from a log.
+ *
+ * Section "Asynchronous Island-model Genetic Algorithm": every island keeps,
+ * per cardinal neighbour, an emigration buffer of one genome and an
+ * immigration buffer of four; each has a completion flag set when its
+ * asynchronous send or receive finishes, and the main cycle first copies
+ * every completed immigration buffer into the population over randomly
+ * chosen members (then re-opens the receive), then refills every completed
+ * emigration buffer with a randomly sampled member (then re-opens the send),
+ * then evaluates, selects and mutates.  Reading used here, per island and
+ * direction d (N, E, S, W), at each migrating generation G of the island:
+ *
+ *   receive : the channel from the neighbour in direction d holds at most one
+ *             genome in flight, numbered by its post count.  If the island
+ *             takes it (a property of timing, hence logged), it must be the
+ *             one after the last it took from that channel; it is appended to
+ *             the immigration buffer and acknowledged (the sender's
+ *             send-complete flag).
+ *   place   : for d = N, E, S, W in that order, an immigration buffer holding
+ *             four genomes is copied into the population, genome j over the
+ *             member at slot floor(v_j n / 2^32) of (v_0..v_3) =
+ *             Philox(key; 0xFFFFFFFE, island, G, 1 + d), later over earlier,
+ *             and emptied.
+ *   send    : if the genome last posted toward d has been acknowledged
+ *             (always true before the first post), the island may (logged)
+ *             post a copy of the member at slot floor(w_d n / 2^32) of
+ *             (w_0..w_3) = Philox(key; 0xFFFFFFFF, island, G, 0), taken after
+ *             placement.
+ *   a3-a6   : as orc_island_step (per-genome counters).
+ *
+ * The log has one word per island, generation (relative to G0) and
+ * direction: (post number taken from direction d, or 0) << 1 | (1 if the
+ * island posted toward d).  All channels and buffers start empty at G0.  The
+ * replay runs island generations in any order that respects the log's
+ * causality (a take needs its post, a post needs the acknowledgement of the
+ * previous one) and checks the protocol: takes on a channel are numbered
+ * 1, 2, 3, ... and a post is never logged before its acknowledgement.
+ *
+ * trait, surf, tcount: the population at G0 (updated in place).  chan (may
+ * be NULL) receives per island and direction {posts made toward d, last post
+ * number taken from d, genomes waiting in the immigration buffer}; inbuf
+ * (may be NULL) the waiting genomes, 4 x {trait, lo, hi, T} per island and
+ * direction.  Returns 0, -1 on allocation failure, -3 if the log breaks the
+ * protocol or cannot be ordered causally. */
+int orc_run_buffered(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
+                     uint32_t *tcount, uint64_t G0, uint32_t n_gens,
+                     const uint32_t *log, uint32_t *chan, uint32_t *inbuf) {
+  uint32_t I = cfg->rows * cfg->cols, n = cfg->n;
+  size_t C = (size_t)I * 4;
+  uint32_t *mail = calloc(C * 4, sizeof(uint32_t));      /* genome in flight */
+  uint32_t *posts = calloc(C, sizeof(uint32_t));         /* by (island, d) */
+  uint32_t *taken = calloc(C, sizeof(uint32_t));         /* from (island, d) */
+  uint32_t *count = calloc(C, sizeof(uint32_t));
+  uint32_t *buf = calloc(C * 16, sizeof(uint32_t));
+  uint32_t *done = calloc(I, sizeof(uint32_t));
+  if (!mail || !posts || !taken || !count || !buf || !done) {
+    free(mail); free(posts); free(taken); free(count); free(buf); free(done);
+    return -1;
+  }
+  int status = 0;
+  uint64_t remaining = (uint64_t)I * n_gens;
+  while (remaining > 0 && status == 0) {
+    int progress = 0;
+    for (uint32_t i = 0; i < I && status == 0; ++i) {
+      uint32_t g = done[i];
+      if (g >= n_gens) continue;
+      uint64_t G = G0 + g;
+      const uint32_t *e = log + ((size_t)i * n_gens + g) * 4;
+      int mig = orc_migrates(cfg, G);
+      uint32_t nb[4], back[4];
+      for (uint32_t d = 0; d < 4; ++d) {
+        nb[d] = orc_neighbour(cfg, i, d);
+        back[d] = (d + 2) % 4;
+        if (!mig && e[d]) status = -3;
+      }
+      if (status) break;
+      /* causality: each take needs its post, each post the acknowledgement
+       * of the previous one (possibly by this very generation's take, when
+       * the island is its own neighbour) */
+      int ready = 1;
+      for (uint32_t d = 0; d < 4; ++d) {
+        uint32_t k = e[d] >> 1;
+        if (k && posts[(size_t)nb[d] * 4 + back[d]] < k) ready = 0;
+        if (e[d] & 1u) {
+          uint32_t r = nb[d], rd = back[d];
+          uint32_t ack = taken[(size_t)r * 4 + rd];
+          if (r == i && (e[rd] >> 1)) ack = e[rd] >> 1;
+          if (ack < posts[(size_t)i * 4 + d]) ready = 0;
+        }
+      }
+      if (!ready) continue;
+      if (mig) {
+        /* receive */
+        for (uint32_t d = 0; d < 4 && status == 0; ++d) {
+          uint32_t k = e[d] >> 1;
+          if (!k) continue;
+          size_t c = (size_t)nb[d] * 4 + back[d], me = (size_t)i * 4 + d;
+          if (k != taken[me] + 1 || posts[c] != k || count[me] >= 4) {
+            status = -3;
+            break;
+          }
+          memcpy(buf + (me * 4 + count[me]) * 4, mail + c * 4, 4 * sizeof(uint32_t));
+          count[me] += 1;
+          taken[me] = k;
+        }
+        if (status) break;
+        /* place */
+        for (uint32_t d = 0; d < 4; ++d) {
+          size_t me = (size_t)i * 4 + d;
+          if (count[me] < 4) continue;
+          uint32_t v[4];
+          orc_draw(cfg->seed, 0xFFFFFFFEu, i, (uint32_t)G, 1 + d, v);
+          for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t *h = buf + (me * 4 + j) * 4;
+            size_t a = (size_t)i * n + orc_index(v[j], n);
+            trait[a] = h[0];
+            surf[a] = (uint64_t)h[1] | ((uint64_t)h[2] << 32);
+            tcount[a] = h[3];
+          }
+          count[me] = 0;
+        }
+        /* send */
+        uint32_t w[4];
+        orc_draw(cfg->seed, 0xFFFFFFFFu, i, (uint32_t)G, 0, w);
+        for (uint32_t d = 0; d < 4; ++d) {
+          if (!(e[d] & 1u)) continue;
+          size_t me = (size_t)i * 4 + d;
+          size_t a = (size_t)i * n + orc_index(w[d], n);
+          mail[me * 4 + 0] = trait[a];
+          mail[me * 4 + 1] = (uint32_t)surf[a];
+          mail[me * 4 + 2] = (uint32_t)(surf[a] >> 32);
+          mail[me * 4 + 3] = tcount[a];
+          posts[me] += 1;
+        }
+      }
+      if (orc_island_step(cfg, i, G, trait, surf, tcount)) { status = -1; break; }
+      done[i] = g + 1;
+      --remaining;
+      progress = 1;
+    }
+    if (!progress && status == 0) status = -3;
+  }
+  if (status == 0 && chan)
+    for (size_t c = 0; c < C; ++c) {
+      chan[3 * c] = posts[c];
+      chan[3 * c + 1] = taken[c];
+      chan[3 * c + 2] = count[c];
+    }
+  if (status == 0 && inbuf) memcpy(inbuf, buf, C * 16 * sizeof(uint32_t));
+  free(mail); free(posts); free(taken); free(count); free(buf); free(done);
   return status;
 }
