@@ -485,10 +485,12 @@ def run_served(args):
         "dtype": "u32", "data": "synthetic"}), flush=True)
 
 
-def run_async_wafer(args):
+def run_async_wafer(args, mode="async"):
     """Free-running migration on the wafer-shaped grid, advanced in slices of
     K generations per launch (each island is loaded once and stored once per
-    slice; within a slice islands never wait for one another)."""
+    slice; within a slice islands never wait for one another).  mode "async":
+    latest-emigrant records; "buffered": the per-neighbour send and receive
+    buffers."""
     import torch
     from paper_2404_10861_gb300 import _build, binding as hb
     _build.build()
@@ -497,7 +499,7 @@ def run_async_wafer(args):
     stream = torch.cuda.Stream()
     out = []
     for K in args.slices:
-        with hb.Grid(stream=stream.cuda_stream, mode="async", seed=1, **WORKLOAD) as g:
+        with hb.Grid(stream=stream.cuda_stream, mode=mode, seed=1, **WORKLOAD) as g:
             for _ in range(args.warmup):
                 g.run(K)
             g.sync()
@@ -512,10 +514,12 @@ def run_async_wafer(args):
         gens = steps * K
         out.append({"generations_per_launch": K, "generations": gens,
                     "value": AGENTS * gens / (ms / 1e3), "us_per_generation": ms * 1e3 / gens})
+    label = {"async": "free-running migration, latest-emigrant records",
+             "buffered": "free-running migration, per-neighbour buffers"}[mode]
     print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
-                      "workload": "wafer-shaped island GA, free-running migration "
+                      "workload": f"wafer-shaped island GA, {label} "
                                   "(512x1024 islands x 32 agents)",
-                      "config": dict(WORKLOAD, mode="async"), "slices": out, "dtype": "u32",
+                      "config": dict(WORKLOAD, mode=mode), "slices": out, "dtype": "u32",
                       "data": "synthetic"}), flush=True)
 
 
@@ -544,7 +548,7 @@ def main():
                     help="profiling mode: only run this many generations of the workload "
                          "(no timing); used for ncu captures")
     ap.add_argument("--workload", default="wafer",
-                    choices=["wafer", "tiny", "mid", "batched", "served", "async"],
+                    choices=["wafer", "tiny", "mid", "batched", "served", "async", "buffered"],
                     help="wafer: the benchmark line; the others: informational lines")
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--memory-cap-mb", type=int, default=2048,
@@ -556,8 +560,8 @@ def main():
     ap.add_argument("--async-gens", type=int, default=2048,
                     help="async workload: timed generations per slice length")
     args = ap.parse_args()
-    if args.workload == "async":
-        run_async_wafer(args)
+    if args.workload in ("async", "buffered"):
+        run_async_wafer(args, args.workload)
         return
     if args.workload == "batched":
         run_batched(args)

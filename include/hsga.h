@@ -96,16 +96,29 @@ typedef enum hsga_kernel {
 } hsga_kernel;
 
 /* Migration modes.  Synchronous: every island takes its neighbours' emigrants
- * of the same generation (bit-reproducible).  Free-running: islands never
- * wait for one another; each takes a neighbour's latest emigrant if it is new
- * and aimed at it (the WSE's own regime, section "Asynchronous Island-model
- * Genetic Algorithm"); results depend on timing, genomes carry their own
- * deposition counters, and agents_per_island <= 32, deposit_interval <= 1.
+ * of the same generation (bit-reproducible).  The two free-running modes are
+ * the WSE's own regime (section "Asynchronous Island-model Genetic
+ * Algorithm"): islands never wait for one another, results depend on timing,
+ * genomes carry their own deposition counters, and agents_per_island <= 32,
+ * deposit_interval <= 1.
+ *   ASYNC: each island publishes one emigrant per migrating generation, aimed
+ *     at a random neighbour, and takes a neighbour's latest emigrant if it is
+ *     new and aimed at it (records overwritten unseen are lost).
+ *   BUFFERED: the paper's per-neighbour buffers.  Per island and direction a
+ *     one-genome send channel and a four-genome receive buffer: at each
+ *     migrating generation an island takes the next genome waiting on each
+ *     incoming channel (acknowledging it), copies every full receive buffer
+ *     into the population over random members (directions N, E, S, W; slots
+ *     from Philox(key; 0xFFFFFFFE, island, G, 1 + d)), then sends a copy of a
+ *     random member (slot from word d of Philox(key; 0xFFFFFFFF, island, G,
+ *     0)) on every channel whose previous genome was acknowledged.  No genome
+ *     is lost; a slow receiver holds its sender back.
  * Free-running grids do not support hsga_migrate, checkpoints, batches or the
  * allocation-free entry point. */
 typedef enum hsga_migration_mode {
   HSGA_MIGRATION_SYNC = 0,
-  HSGA_MIGRATION_ASYNC = 1
+  HSGA_MIGRATION_ASYNC = 1,
+  HSGA_MIGRATION_BUFFERED = 2
 } hsga_migration_mode;
 
 /* Run configuration (plain data, caller-owned; copied by hsga_init_grid). */
@@ -216,16 +229,29 @@ int hsga_get_fossils(hsga_grid *g, uint32_t *out_words, uint32_t *out_island_slo
 int hsga_get_counters(hsga_grid *g, uint32_t *T_out);
 
 /* Free-running grids: logs, for the next `generations` generations from the
- * current one, which neighbour emigrant each island took: entry
- * ((island * generations + g) * 4 + d) holds 1 + the absolute generation of
- * the emigrant taken from direction d at generation G_now + g, or 0.  Starts
- * a fresh free-running window (no record published earlier is taken), so the
- * CPU oracle can replay the window exactly.  generations = 0 stops logging. */
+ * current one, what each island exchanged; entry ((island * generations + g)
+ * * 4 + d) describes direction d at generation G_now + g.  ASYNC: 1 + the
+ * absolute generation of the emigrant taken from direction d, or 0.
+ * BUFFERED: (number of the post taken from direction d, counted from 1 on
+ * each channel, or 0) << 1 | (1 if the island sent toward d).  Starts a fresh
+ * free-running window (no record published earlier is taken; buffered
+ * channels and receive buffers are emptied), so the CPU oracle can replay the
+ * window exactly.  generations = 0 stops logging. */
 int hsga_set_async_log(hsga_grid *g, uint32_t generations);
 
 /* Copies the log (islands * generations * 4 uint32; host or device).
  * Synchronous. */
 int hsga_get_async_log(hsga_grid *g, uint32_t *out);
+
+/* BUFFERED grids: channel state.  chan_out (islands * 4 * 3 uint32) receives
+ * per island and direction {posts sent toward d, number of the last post
+ * taken from d, genomes waiting in the receive buffer of d}; inbuf_out (may be
+ * NULL; islands * 4 * 4 * 4 uint32) the receive buffers, 4 genomes
+ * {trait, surface low, surface high, T} per island and direction, of which
+ * the first `waiting` are meaningful.  Counts restart at every
+ * hsga_set_async_log.  Host or device; synchronous.  HSGA_ERR_UNSUPPORTED for
+ * other modes. */
+int hsga_get_migration_buffers(hsga_grid *g, uint32_t *chan_out, uint32_t *inbuf_out);
 
 /* Waits for the grid's stream and returns the first error a kernel reported
  * (HSGA_ERR_WAIT_TIMEOUT, HSGA_ERR_DEVICE) or a pending CUDA error. */

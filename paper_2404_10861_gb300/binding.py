@@ -89,6 +89,8 @@ _SIGS = {
     "hsga_get_counters": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "hsga_set_async_log": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "hsga_get_async_log": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hsga_get_migration_buffers": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                                   ctypes.c_int),
     "hsga_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_stats)], ctypes.c_int),
     "hsga_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
@@ -199,7 +201,7 @@ def make_config(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2
                 coarsen=1, mode="sync") -> hsga_config:
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return hsga_config(rows, cols, n, tournament, pol, bits, W, interval, p_ben, p_del,
-                       seed, kernel, coarsen, {"sync": 0, "async": 1}[mode], 0)
+                       seed, kernel, coarsen, {"sync": 0, "async": 1, "buffered": 2}[mode], 0)
 
 
 def hsga_init_grid(cfg: hsga_config, cuda_stream=None) -> ctypes.c_void_p:
@@ -259,6 +261,17 @@ def hsga_get_async_log(g, islands: int, generations: int) -> np.ndarray:
     out = np.zeros((islands, generations, 4), dtype=np.uint32)
     _check(lib().hsga_get_async_log(g, _ptr(out)), "hsga_get_async_log")
     return out
+
+
+def hsga_get_migration_buffers(g, islands: int):
+    """Buffered grids: (chan, inbuf) with chan[island, d] = (posts sent toward
+    d, last post taken from d, genomes waiting) and inbuf[island, d, j] =
+    (trait, surface lo, surface hi, T) of waiting genome j."""
+    chan = np.zeros((islands, 4, 3), dtype=np.uint32)
+    inbuf = np.zeros((islands, 4, 4, 4), dtype=np.uint32)
+    _check(lib().hsga_get_migration_buffers(g, _ptr(chan), _ptr(inbuf)),
+           "hsga_get_migration_buffers")
+    return chan, inbuf
 
 
 def hsga_synchronize(g):
@@ -463,6 +476,9 @@ class Grid:
 
     def run(self, n):
         hsga_run_generations(self.handle, n)
+
+    def buffers(self):
+        return hsga_get_migration_buffers(self.handle, self.islands)
 
     def migrate(self):
         hsga_migrate(self.handle)

@@ -49,9 +49,17 @@ struct hsga_grid {
   uint32_t *fossil_where = nullptr;  // fossil_cap x 2
   // free-running migration: per-genome counters, last stamp seen per
   // (island, direction), optional take log
-  bool async = false;
+  bool async = false;     // either free-running mode
+  bool buffered = false;  // per-neighbour buffers
   uint32_t *tcount = nullptr;
   uint32_t *seen = nullptr;
+  // buffered mode, per island and direction: the channel's genome in flight
+  // (4 self-stamped words), its acknowledgement, the receive buffer and the
+  // lane state {posts, taken, waiting, 0}
+  uint64_t *mail = nullptr;
+  uint32_t *ack = nullptr;
+  uint4 *inbuf = nullptr;
+  uint4 *chst = nullptr;
   uint32_t *alog = nullptr;
   uint32_t alog_gens = 0;
   uint64_t alog_G0 = 0;
@@ -119,8 +127,8 @@ int validate(const hsga_config *c) {
   if (!(c->p_deleterious >= 0.0 && c->p_deleterious <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
   if (c->kernel > HSGA_KERNEL_RESIDENT_GRID || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
-  if (c->migration_mode > HSGA_MIGRATION_ASYNC) return HSGA_ERR_INVALID_ARG;
-  if (c->migration_mode == HSGA_MIGRATION_ASYNC &&
+  if (c->migration_mode > HSGA_MIGRATION_BUFFERED) return HSGA_ERR_INVALID_ARG;
+  if (c->migration_mode != HSGA_MIGRATION_SYNC &&
       (c->agents_per_island > 32 || c->deposit_interval > 1))
     return HSGA_ERR_INVALID_ARG;
   return HSGA_OK;
@@ -189,6 +197,10 @@ void free_grid(hsga_grid *g) {
   dev_free(g->alloc, g->fossil_where, g->stream);
   dev_free(g->alloc, g->tcount, g->stream);
   dev_free(g->alloc, g->seen, g->stream);
+  dev_free(g->alloc, g->mail, g->stream);
+  dev_free(g->alloc, g->ack, g->stream);
+  dev_free(g->alloc, g->inbuf, g->stream);
+  dev_free(g->alloc, g->chst, g->stream);
   dev_free(g->alloc, g->alog, g->stream);
   cudaStreamSynchronize(g->stream);
   delete g;
@@ -212,8 +224,20 @@ cudaError_t fill_u32(uint32_t *dst, uint32_t value, uint64_t count, cudaStream_t
   return cudaGetLastError();
 }
 
+// Empties the buffered mode's channels: nothing in flight, nothing waiting,
+// post numbers restart at 1.
+cudaError_t reset_channels(hsga_grid *g) {
+  if (!g->buffered) return cudaSuccess;
+  const size_t C = 4 * (size_t)g->p.islands;
+  cudaError_t e = cudaMemsetAsync(g->mail, 0, sizeof(uint64_t) * 4 * C, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->ack, 0, sizeof(uint32_t) * C, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->chst, 0, sizeof(uint4) * C, g->stream);
+  return e;
+}
+
 int reset_sync_state(hsga_grid *g) {
   cudaError_t e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+  if (e == cudaSuccess) e = reset_channels(g);
   if (e == cudaSuccess && g->async)
     e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess && g->seen)
@@ -270,12 +294,21 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
                          : nullptr;
   }
   g->rec = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
-  g->async = cfg->migration_mode == HSGA_MIGRATION_ASYNC;
+  g->async = cfg->migration_mode != HSGA_MIGRATION_SYNC;
+  g->buffered = cfg->migration_mode == HSGA_MIGRATION_BUFFERED;
   if (g->async) {
+    const size_t C = 4 * (size_t)g->p.islands;
     g->tcount = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->agents, g->stream);
-    g->seen = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * 4 * (size_t)g->p.islands,
-                                    g->stream);
-    if (!g->tcount || !g->seen) {
+    g->seen = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * C, g->stream);
+    bool ok = g->tcount && g->seen;
+    if (g->buffered) {
+      g->mail = (uint64_t *)dev_alloc(g->alloc, sizeof(uint64_t) * 4 * C, g->stream);
+      g->ack = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * C, g->stream);
+      g->inbuf = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 4 * C, g->stream);
+      g->chst = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * C, g->stream);
+      ok = ok && g->mail && g->ack && g->inbuf && g->chst;
+    }
+    if (!ok) {
       free_grid(g);
       return HSGA_ERR_OOM;
     }
@@ -412,7 +445,17 @@ int hsga_run_generations(hsga_grid *g, uint64_t n) {
 namespace {
 int advance(hsga_grid *g, uint64_t n) {
   cudaError_t e = cudaSuccess;
-  if (g->async) {
+  if (g->buffered) {
+    const uint64_t slice = 1u << 16;
+    for (uint64_t done = 0; done < n && e == cudaSuccess;) {
+      const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
+      e = launch_step_buffered(g->p, (uint32_t)(g->G + done), m, g->trait[g->cur],
+                               g->surf[g->cur], g->tcount, g->mail, g->ack, g->inbuf, g->chst,
+                               g->alog, (uint32_t)g->alog_G0, g->alog_gens, g->stream);
+      g->launches++;
+      done += m;
+    }
+  } else if (g->async) {
     const uint64_t slice = 1u << 16;
     for (uint64_t done = 0; done < n && e == cudaSuccess;) {
       const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
@@ -527,6 +570,7 @@ int hsga_set_async_log(hsga_grid *g, uint32_t generations) {
     e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
+  if (e == cudaSuccess) e = reset_channels(g);
   g->alog_gens = generations;
   g->alog_G0 = g->G;
   return cuda_status(e);
@@ -538,6 +582,20 @@ int hsga_get_async_log(hsga_grid *g, uint32_t *out) {
   cudaError_t e = cudaMemcpyAsync(out, g->alog,
                                   sizeof(uint32_t) * 4 * (size_t)g->p.islands * g->alog_gens,
                                   cudaMemcpyDefault, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  return cuda_status(e);
+}
+
+int hsga_get_migration_buffers(hsga_grid *g, uint32_t *chan_out, uint32_t *inbuf_out) {
+  if (!g || !chan_out) return HSGA_ERR_INVALID_ARG;
+  if (!g->buffered) return HSGA_ERR_UNSUPPORTED;
+  const size_t C = 4 * (size_t)g->p.islands;
+  // {posts, taken, waiting, 0} per channel -> 3 words per channel
+  cudaError_t e = cudaMemcpy2DAsync(chan_out, 3 * sizeof(uint32_t), g->chst, sizeof(uint4),
+                                    3 * sizeof(uint32_t), C, cudaMemcpyDefault, g->stream);
+  if (e == cudaSuccess && inbuf_out)
+    e = cudaMemcpyAsync(inbuf_out, g->inbuf, sizeof(uint4) * 4 * C, cudaMemcpyDefault,
+                        g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   return cuda_status(e);
 }

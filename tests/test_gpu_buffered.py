@@ -1,0 +1,143 @@
+"""Buffered free-running migration (the WSE's per-neighbour buffers) on the GPU.
+
+Which genome each island takes, and when it sends, depends on timing, so a
+run is not reproducible; given the log of its takes and sends it is
+deterministic.  The oracle replays the GPU's own log and must reproduce every
+trait, surface, per-genome counter, channel count and waiting genome
+bit-exactly -- on single runs of several shapes, and on every one of 32
+replicates, so the distribution of outcomes (fitness, phylometrics) over
+replicates is the oracle's exactly.  The replay also checks the protocol on
+the GPU's log: takes on a channel are numbered 1, 2, 3, ... and no genome is
+sent before the previous one was acknowledged.
+"""
+import numpy as np
+import pytest
+
+from oracle import phylo
+from paper_2404_10861_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_10861_gb300 import _build, binding
+    _build.build()
+    return binding
+
+
+def ocfg(orc, kw):
+    pol = orc.POLICY_NAMES[kw.get("policy", "steady")]
+    return orc.Config(rows=kw["rows"], cols=kw["cols"], n=kw["n"],
+                      tournament=kw.get("tournament", 2), policy=pol, bits=kw.get("bits", 1),
+                      W=kw.get("W", 2), interval=kw.get("interval", 1),
+                      p_ben=kw.get("p_ben", 0.0), p_del=kw.get("p_del", 0.0), seed=kw["seed"])
+
+
+def run_logged(hb, kw, trait, surf, G0, chunks):
+    gens = sum(chunks)
+    with hb.Grid(mode="buffered", **kw) as g:
+        g.set_population(trait, surf, G0)
+        hb.hsga_set_async_log(g.handle, gens)
+        for c in chunks:
+            g.run(c)
+        g.sync()
+        t, s = g.population()
+        T = g.counters()
+        log = hb.hsga_get_async_log(g.handle, kw["rows"] * kw["cols"], gens)
+        chan, inbuf = g.buffers()
+    return t, s, T, log, chan, inbuf
+
+
+def same_buffers(chan, inbuf, ochan, obuf):
+    waiting = np.arange(4)[None, None, :] < ochan[:, :, 2:3]
+    return np.array_equal(chan, ochan) and np.array_equal(inbuf[waiting], obuf[waiting])
+
+
+CASES = [
+    dict(rows=8, cols=8, n=32, tournament=2, policy="tilted", bits=1, p_ben=0.01, seed=1),
+    dict(rows=16, cols=12, n=24, tournament=5, policy="hybrid", bits=2, p_ben=0.02, p_del=0.01,
+         seed=2),
+    dict(rows=1, cols=6, n=17, tournament=1, policy="steady", bits=4, seed=3),
+    dict(rows=5, cols=5, n=32, tournament=3, policy="stretched", bits=1, interval=3, seed=4),
+    dict(rows=64, cols=64, n=32, tournament=2, policy="tilted", bits=2, p_ben=1e-3, seed=5),
+    dict(rows=1, cols=1, n=1, tournament=1, policy="none", p_ben=1.0, seed=6),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_buffered_run_replays_exactly(hb, orc, case):
+    kw = CASES[case]
+    c = ocfg(orc, kw)
+    trait, surf = inputs.small_trait_population(c.agents, seed=case, levels=4)
+    if c.policy == orc.NONE:
+        surf = np.zeros_like(surf)                        # an untracked grid has no surfaces
+    G0 = 100
+    chunks = (60, 140) if case != 4 else (200,)
+    t, s, T, log, chan, inbuf = run_logged(hb, kw, trait, surf, G0, chunks)
+    gens = sum(chunks)
+    ot, os_, oT, ochan, obuf = orc.run_buffered(c, trait, surf,
+                                                np.full(c.agents, G0, np.uint32), G0, gens, log)
+    assert np.array_equal(t, ot) and np.array_equal(s, os_) and np.array_equal(T, oT)
+    assert same_buffers(chan, inbuf, ochan, obuf)
+    assert T.min() >= G0
+    takes = int(((log >> 1) > 0).sum())
+    assert takes > 0 and (chan[:, :, 1] >= 4).any()        # buffers filled and were placed
+    # no genome is lost: all posts but the one in flight were taken
+    for i in range(c.islands):
+        for d in range(4):
+            nb = orc.neighbour(c, i, d)
+            assert int(chan[i, d, 0]) - int(chan[nb, (d + 2) % 4, 1]) in (0, 1)
+
+
+def summary(c, t, s, T):
+    """Mean trait and phylometrics of 48 sampled genomes sharing the modal
+    counter (genomes carry their own counters in free-running modes)."""
+    Tm = np.bincount(T).argmax()
+    pool = s[T == Tm]
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(pool), size=min(48, len(pool)), replace=False)
+    m = phylo.phylometrics(phylo.reconstruct(pool[pick], c.policy, c.bits, c.W, int(Tm)))
+    return [float(t.mean()), m["mean_pairwise_distance"], m["sackin"], m["colless"]]
+
+
+def test_buffered_replicates_replay_exactly(hb, orc):
+    kw = dict(rows=8, cols=8, n=32, tournament=2, policy="tilted", bits=1, p_ben=5e-3)
+    gens, reps = 300, 32
+    gpu, ora, immigrants = [], [], 0
+    for r in range(reps):
+        kwr = dict(kw, seed=100 + r)
+        c = ocfg(orc, kwr)
+        trait, surf = inputs.founders(c.agents)
+        t, s, T, log, chan, inbuf = run_logged(hb, kwr, trait, surf, 0, (gens,))
+        ot, os_, oT, ochan, obuf = orc.run_buffered(c, trait, surf, np.zeros(c.agents, np.uint32),
+                                                    0, gens, log)
+        assert np.array_equal(t, ot) and np.array_equal(s, os_) and np.array_equal(T, oT), r
+        assert same_buffers(chan, inbuf, ochan, obuf), r
+        gpu.append(summary(c, t, s, T))
+        ora.append(summary(c, ot, os_, oT))
+        immigrants += int(((log >> 1) > 0).sum())
+    gpu, ora = np.array(gpu), np.array(ora)
+    assert np.array_equal(gpu, ora)                       # identical distributions
+    rate = immigrants / (reps * 64 * gens)
+    assert 0 < rate <= 4.0
+    print(f"buffered: immigrants per island-generation {rate:.3f}; mean trait "
+          f"{gpu[:, 0].mean():.2f}; mean pairwise distance {gpu[:, 1].mean():.1f}")
+
+
+def test_buffered_log_window_restarts_channels(hb):
+    kw = dict(rows=4, cols=4, n=8, tournament=2, policy="tilted", bits=1, seed=9)
+    with hb.Grid(mode="buffered", **kw) as g:
+        g.run(50)
+        chan, _ = g.buffers()
+        assert chan[:, :, 0].max() > 0
+        hb.hsga_set_async_log(g.handle, 10)
+        g.sync()
+        chan, _ = g.buffers()
+        assert not chan.any()                             # a fresh window
+        g.run(10)
+        log = hb.hsga_get_async_log(g.handle, 16, 10)
+        assert (log[:, 0, :] & 1).all()                   # every channel sends at once
