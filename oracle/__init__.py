@@ -28,14 +28,16 @@ STEADY, TILTED, STRETCHED, TRIVIAL, NONE, HYBRID = 0, 1, 2, 3, 4, 5
 POLICY_NAMES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
                 "trivial": TRIVIAL, "none": NONE, "hybrid": HYBRID}
 REC_WORDS = 6
+FITNESS_TRAIT, FITNESS_FLOAT = 0, 1
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable C: x86_64 and aarch64)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        # -ffp-contract=off: every float operation is rounded on its own
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -47,7 +49,7 @@ class _Cfg(ctypes.Structure):
                 ("W", ctypes.c_uint32), ("interval", ctypes.c_uint32),
                 ("p_ben", ctypes.c_double), ("p_del", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("coarsen", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("fitness", ctypes.c_uint32), ("sigma", ctypes.c_double)]
 
 
 @dataclass
@@ -59,7 +61,9 @@ class Config:
     sites per level W (tilted / stretched), migration interval (0 = none),
     beneficial / deleterious mutation probabilities, the Philox seed, and
     the annotation interval (temporal coarsening: deposit every coarsen-th
-    generation).
+    generation), and the fitness model: FITNESS_TRAIT (unsigned integer,
+    mutations of one) or FITNESS_FLOAT (binary32, sign-restricted Gaussian
+    mutation amounts of standard deviation ``sigma``).
     """
     rows: int = 4
     cols: int = 4
@@ -73,6 +77,8 @@ class Config:
     p_del: float = 0.0
     seed: int = 1
     coarsen: int = 1
+    fitness: int = 0
+    sigma: float = 1.0
 
     @property
     def islands(self) -> int:
@@ -89,7 +95,7 @@ class Config:
     def _c(self) -> _Cfg:
         return _Cfg(self.rows, self.cols, self.n, self.tournament, self.policy,
                     self.bits, self.W, self.interval, self.p_ben, self.p_del,
-                    self.seed, self.coarsen, 0)
+                    self.seed, self.coarsen, self.fitness, self.sigma)
 
 
 _lib = None

@@ -66,6 +66,7 @@
  * Timestamp lookup is written as its definition: the last deposition time
  * below T whose site is p, found by replaying the site function (brute force).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -208,8 +209,81 @@ typedef struct orc_cfg {
   double p_ben, p_del;
   uint64_t seed;
   uint32_t coarsen; /* annotate every coarsen-th generation (0 or 1: every one) */
-  uint32_t pad;
+  uint32_t fitness; /* ORC_FITNESS_TRAIT or ORC_FITNESS_FLOAT */
+  double sigma;     /* ORC_FITNESS_FLOAT: standard deviation of the mutation amount */
 } orc_cfg;
+
+/* Fitness models ("Methods › Genome Model" and "Results › On-hardware
+ * Trial").  TRAIT: the first genome word is an unsigned integer fitness and
+ * mutation adds or removes one (saturating).  FLOAT: the first word is an
+ * IEEE binary32 fitness (the paper's 128-bit layout) and mutation adds
+ * (beneficial) or subtracts (deleterious) the absolute value of a normally
+ * distributed amount -- the paper's Gaussian mutation with sign restrictions.
+ * The normal variate is the de Moivre-Laplace approximation: with (q0..q3) =
+ * Philox(key; j, island, G, ORC_PURPOSE_GAUSS), B = popcount(q0) +
+ * popcount(q1) + popcount(q2) ~ Binomial(96, 1/2) (mean 48, variance 24) is
+ * smoothed by U = bits 8..31 of q3 / 2^24 (uniform, variance 1/12):
+ *   g = (B - 48) 2^24 + (q3 >> 8) - 2^23          (exact, in int32)
+ *   amount = |float(g) * c|,  c = float(sigma / sqrt(24 + 1/12) / 2^24),
+ * so amount / sigma is |N(0, 1)| to within the approximation.  Every float
+ * step is one correctly rounded IEEE operation (int-to-float, multiply,
+ * add), evaluated without contraction, so any IEEE machine gets the same
+ * bits.  Tournament candidates compare as floats; a later candidate wins only
+ * if strictly fitter (the paper breaks ties at random; the first of several
+ * equally fit candidates drawn uniformly at random is itself uniformly
+ * random among them). */
+enum { ORC_FITNESS_TRAIT = 0, ORC_FITNESS_FLOAT = 1 };
+#define ORC_PURPOSE_GAUSS 256u
+
+static float orc_f32(uint32_t w) {
+  float f;
+  memcpy(&f, &w, sizeof f);
+  return f;
+}
+
+static uint32_t orc_u32(float f) {
+  uint32_t w;
+  memcpy(&w, &f, sizeof w);
+  return w;
+}
+
+static uint32_t orc_popcount(uint32_t x) {
+  uint32_t c = 0;
+  for (; x; x >>= 1) c += x & 1u;
+  return c;
+}
+
+/* a3 + a4: is the genome with first word a strictly fitter than b's? */
+static int orc_fitter(const orc_cfg *cfg, uint32_t a, uint32_t b) {
+  if (cfg->fitness == ORC_FITNESS_FLOAT) return orc_f32(a) > orc_f32(b);
+  return a > b;
+}
+
+static uint64_t orc_threshold(double p);
+
+/* a5: mutation of child j of `island` at generation G whose parent's first
+ * word is `trait`; w2 is word 2 of the child's replication block. */
+static uint32_t orc_mutate(const orc_cfg *cfg, uint32_t trait, uint32_t w2,
+                           uint32_t j, uint32_t island, uint64_t G) {
+  uint64_t thr_b = orc_threshold(cfg->p_ben), thr_d = orc_threshold(cfg->p_del);
+  int ben = (uint64_t)w2 < thr_b;
+  int del = !ben && (uint64_t)w2 < thr_b + thr_d;
+  if (cfg->fitness != ORC_FITNESS_FLOAT) {
+    if (ben && trait != 0xFFFFFFFFu) return trait + 1;
+    if (del && trait != 0) return trait - 1;
+    return trait;
+  }
+  if (!ben && !del) return trait;
+  uint32_t q[4];
+  orc_draw(cfg->seed, j, island, (uint32_t)G, ORC_PURPOSE_GAUSS, q);
+  int32_t B = (int32_t)(orc_popcount(q[0]) + orc_popcount(q[1]) + orc_popcount(q[2]));
+  int32_t g = (B - 48) * (1 << 24) + (int32_t)(q[3] >> 8) - (1 << 23);
+  float c = (float)(cfg->sigma / sqrt(24.0 + 1.0 / 12.0) / 16777216.0);
+  float amount = fabsf((float)g * c);
+  float f = orc_f32(trait);
+  f = ben ? f + amount : f - amount;
+  return orc_u32(f);
+}
 
 enum { ORC_N = 0, ORC_E = 1, ORC_S = 2, ORC_W = 3 };
 
@@ -292,8 +366,6 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
                 uint64_t T, uint32_t *trait_out, uint64_t *surf_out,
                 uint64_t *parent_out) {
   uint32_t n = cfg->n;
-  uint64_t thr_b = orc_threshold(cfg->p_ben);
-  uint64_t thr_d = orc_threshold(cfg->p_del);
   uint32_t S = 64 / cfg->bits;
   /* Temporal coarsening (the paper's suggestion to update annotations only
    * every k-th generation): generation T deposits only when k divides it,
@@ -323,17 +395,12 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
           word = extra[(c - 2) % 4];
         }
         uint32_t cand = orc_index(word, n);
-        if (fit[cand] > fit[best]) best = cand;
+        if (orc_fitter(cfg, fit[cand], fit[best])) best = cand;
       }
       size_t pa = (size_t)l * n + best;
-      uint32_t trait = trait_in[pa];
       uint64_t surface = surf_in[pa];
       /* a5: mutation of the trait. */
-      if ((uint64_t)w[2] < thr_b) {
-        if (trait != 0xFFFFFFFFu) trait += 1;
-      } else if ((uint64_t)w[2] < thr_b + thr_d) {
-        if (trait != 0) trait -= 1;
-      }
+      uint32_t trait = orc_mutate(cfg, trait_in[pa], w[2], j, gid[l], G);
       /* a6: deposit the new differentia (the hybrid policy's second one is
        * taken from bits 16.. of the same word). */
       if (cfg->policy != ORC_NONE && site < S) {
@@ -537,7 +604,6 @@ int orc_island_step(const orc_cfg *cfg, uint32_t i, uint64_t G, uint32_t *trait,
   uint32_t n = cfg->n;
   uint32_t S = 64 / cfg->bits;
   uint64_t vmask = (1ull << cfg->bits) - 1;
-  uint64_t thr_b = orc_threshold(cfg->p_ben), thr_d = orc_threshold(cfg->p_del);
   uint32_t *ct = malloc(sizeof(uint32_t) * n), *cT = malloc(sizeof(uint32_t) * n);
   uint64_t *cs = malloc(sizeof(uint64_t) * n);
   if (!ct || !cT || !cs) {
@@ -559,17 +625,12 @@ int orc_island_step(const orc_cfg *cfg, uint32_t i, uint64_t G, uint32_t *trait,
         word = extra[(c - 2) % 4];
       }
       uint32_t cand = orc_index(word, n);
-      if (fit[cand] > fit[best]) best = cand;
+      if (orc_fitter(cfg, fit[cand], fit[best])) best = cand;
     }
     size_t pa = (size_t)i * n + best;
-    uint32_t tr = trait[pa];
+    uint32_t tr = orc_mutate(cfg, trait[pa], w[2], j, i, G);
     uint64_t su = surf[pa];
     uint32_t T = tcount[pa];
-    if ((uint64_t)w[2] < thr_b) {
-      if (tr != 0xFFFFFFFFu) tr += 1;
-    } else if ((uint64_t)w[2] < thr_b + thr_d) {
-      if (tr != 0) tr -= 1;
-    }
     if (cfg->policy != ORC_NONE) {
       uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
       if (site < S) {
