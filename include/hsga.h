@@ -121,6 +121,27 @@ typedef enum hsga_migration_mode {
   HSGA_MIGRATION_BUFFERED = 2
 } hsga_migration_mode;
 
+/* Fitness models (sections "Genome Model" and "On-hardware Trial").
+ *   TRAIT: the genome's first word is an unsigned integer fitness; mutations
+ *     add or remove one (saturating).
+ *   FLOAT: the first word is an IEEE binary32 fitness (the paper's 128-bit
+ *     layout); a beneficial mutation adds, a deleterious one subtracts, the
+ *     absolute value of a normally distributed amount of standard deviation
+ *     mutation_sigma (the paper's Gaussian mutation with sign restrictions).
+ *     The normal variate is the de Moivre-Laplace approximation from child
+ *     j's block (q0..q3) = Philox(key; j, island, G, 256):
+ *       g = (popc(q0) + popc(q1) + popc(q2) - 48) 2^24 + (q3 >> 8) - 2^23,
+ *       amount = |float(g) * c|, c = float(sigma / sqrt(24 + 1/12) / 2^24),
+ *     each float step one correctly rounded operation, so results are
+ *     bit-reproducible.  Candidates compare as floats.  Requires
+ *     agents_per_island <= 32 and the streamed kernel (or AUTO) in
+ *     synchronous mode; not available in batches or the allocation-free
+ *     entry point. */
+typedef enum hsga_fitness {
+  HSGA_FITNESS_TRAIT = 0,
+  HSGA_FITNESS_FLOAT = 1
+} hsga_fitness;
+
 /* Run configuration (plain data, caller-owned; copied by hsga_init_grid). */
 typedef struct hsga_config {
   uint32_t rows, cols;          /* toroidal island grid, each >= 1 */
@@ -138,7 +159,9 @@ typedef struct hsga_config {
                                    k | G deposit, as deposition G / k (0 or 1:
                                    every generation) */
   uint32_t migration_mode;      /* hsga_migration_mode */
-  uint32_t reserved;            /* must be 0 */
+  uint32_t fitness;             /* hsga_fitness */
+  double mutation_sigma;        /* FLOAT: standard deviation of mutation amounts, > 0 */
+  uint64_t reserved;            /* must be 0 */
 } hsga_config;
 
 typedef struct hsga_stats {

@@ -41,7 +41,8 @@ class hsga_config(ctypes.Structure):
                 ("p_beneficial", ctypes.c_double), ("p_deleterious", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
                 ("deposit_interval", ctypes.c_uint32), ("migration_mode", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("fitness", ctypes.c_uint32), ("mutation_sigma", ctypes.c_double),
+                ("reserved", ctypes.c_uint64)]
 
 
 class hsga_stats(ctypes.Structure):
@@ -198,10 +199,14 @@ def use_default_allocator():
 # ------------------------------------------------------------ functions ---
 def make_config(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2,
                 interval=1, p_ben=0.0, p_del=0.0, seed=1, kernel=KERNEL_AUTO,
-                coarsen=1, mode="sync") -> hsga_config:
+                coarsen=1, mode="sync", fitness="trait", sigma=0.0) -> hsga_config:
+    """fitness "trait": unsigned integer fitness, mutations of one; "float":
+    binary32 fitness with sign-restricted Gaussian mutation amounts of
+    standard deviation ``sigma`` (> 0)."""
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return hsga_config(rows, cols, n, tournament, pol, bits, W, interval, p_ben, p_del,
-                       seed, kernel, coarsen, {"sync": 0, "async": 1, "buffered": 2}[mode], 0)
+                       seed, kernel, coarsen, {"sync": 0, "async": 1, "buffered": 2}[mode],
+                       {"trait": 0, "float": 1}[fitness], sigma, 0)
 
 
 def hsga_init_grid(cfg: hsga_config, cuda_stream=None) -> ctypes.c_void_p:

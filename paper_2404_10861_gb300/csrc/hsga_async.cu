@@ -43,8 +43,9 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
 
 // a3-a6 of one island (lane = child slot) when genomes carry their own
 // deposition counters: the child deposits at site(T_parent) and carries
-// T_parent + 1.  t, s, T: this lane's genome, replaced by its child.
-template <bool TRACKED, bool T2, bool TWO>
+// T_parent + 1.  t, s, T: this lane's genome, replaced by its child.  FLT:
+// binary32 fitness with Gaussian mutation amounts.
+template <bool TRACKED, bool T2, bool TWO, bool FLT = false>
 __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, uint32_t isl,
                                              uint32_t G, uint32_t &t, uint64_t &s,
                                              uint32_t &T) {
@@ -57,7 +58,7 @@ __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, 
   if (T2 || p.tournament >= 2) {
     const uint32_t c = uindex(w.y, n);
     const uint32_t fc = fetch32<1>(pt, c);
-    const bool pick = fc > fbest;
+    const bool pick = fitter<FLT>(fc, fbest);
     best = pick ? c : best;
     fbest = pick ? fc : fbest;
   }
@@ -70,7 +71,7 @@ __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, 
         if (c0 + q < p.tournament) {
           const uint32_t c = uindex(ew[q], n);
           const uint32_t fc = fetch32<1>(pt, c);
-          if (fc > fbest) {
+          if (fitter<FLT>(fc, fbest)) {
             best = c;
             fbest = fc;
           }
@@ -78,7 +79,11 @@ __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, 
       }
     }
   }
-  const uint32_t child_t = mutate(p, fbest, w.z);
+  uint32_t child_t;
+  if constexpr (FLT)
+    child_t = mutate_float(p, fbest, w.z, lane, isl, G);
+  else
+    child_t = mutate(p, fbest, w.z);
   const uint32_t Tp = fetch32<1>(pT, best);
   uint64_t child_s = 0;
   if constexpr (TRACKED) {
@@ -92,7 +97,7 @@ __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, 
 
 // IPW islands per warp: lane 4k + j writes word j of island k's record, and
 // lane 4k + d reads the record of island k's neighbour in direction d.
-template <bool TRACKED, bool T2, bool TWO, int IPW>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
 __global__ void __launch_bounds__(kResidentThreads)
     step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                       uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(kResidentThreads)
 #pragma unroll
     for (int k = 0; k < IPW; ++k)
       if (live[k])
-        counter_step<TRACKED, T2, TWO>(p, lane, isl[k], G, pt[k][0], ps[k][0], pT[k][0]);
+        counter_step<TRACKED, T2, TWO, FLT>(p, lane, isl[k], G, pt[k][0], ps[k][0], pT[k][0]);
   }
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
@@ -250,7 +255,7 @@ __device__ __forceinline__ uint32_t pick4(uint32_t a, uint32_t b, uint32_t c, ui
 // receiver acknowledged the previous post.  No waits, no fences.  The lane
 // state {posts, taken, waiting} and the first three buffered genomes persist
 // in global memory between launches; the fourth is placed as it arrives.
-template <bool TRACKED, bool T2, bool TWO, int IPW>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
 __global__ void __launch_bounds__(kResidentThreads)
     step_buffered_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                          uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__(kResidentThreads)
 #pragma unroll
     for (int k = 0; k < IPW; ++k)
       if (live[k])
-        counter_step<TRACKED, T2, TWO>(p, lane, first + k, G, pt[k][0], ps[k][0], pT[k][0]);
+        counter_step<TRACKED, T2, TWO, FLT>(p, lane, first + k, G, pt[k][0], ps[k][0], pT[k][0]);
   }
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
@@ -404,39 +409,112 @@ constexpr int kAsyncIslandsPerWarp = 8;
 using AsyncFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
                          uint64_t *, uint32_t *, uint32_t *, uint32_t, uint32_t);
 
-AsyncFn pick_async(bool tracked, bool t2, bool two) {
+AsyncFn pick_async(bool tracked, bool t2, bool two, bool flt) {
   constexpr int I = kAsyncIslandsPerWarp;
+  if (flt) {  // general tournament path only
+    if (!tracked) return step_async_kernel<false, false, false, I, true>;
+    return two ? step_async_kernel<true, false, true, I, true>
+               : step_async_kernel<true, false, false, I, true>;
+  }
   if (!tracked)
-    return t2 ? step_async_kernel<false, true, false, I> : step_async_kernel<false, false, false, I>;
+    return t2 ? step_async_kernel<false, true, false, I, false>
+              : step_async_kernel<false, false, false, I, false>;
   if (two)
-    return t2 ? step_async_kernel<true, true, true, I> : step_async_kernel<true, false, true, I>;
-  return t2 ? step_async_kernel<true, true, false, I> : step_async_kernel<true, false, false, I>;
+    return t2 ? step_async_kernel<true, true, true, I, false>
+              : step_async_kernel<true, false, true, I, false>;
+  return t2 ? step_async_kernel<true, true, false, I, false>
+            : step_async_kernel<true, false, false, I, false>;
 }
 
 using BufferedFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
                             uint64_t *, uint32_t *, uint4 *, uint4 *, uint32_t *, uint32_t,
                             uint32_t);
 
-BufferedFn pick_buffered(bool tracked, bool t2, bool two) {
+BufferedFn pick_buffered(bool tracked, bool t2, bool two, bool flt) {
   constexpr int I = kAsyncIslandsPerWarp;
+  if (flt) {  // general tournament path only
+    if (!tracked) return step_buffered_kernel<false, false, false, I, true>;
+    return two ? step_buffered_kernel<true, false, true, I, true>
+               : step_buffered_kernel<true, false, false, I, true>;
+  }
   if (!tracked)
-    return t2 ? step_buffered_kernel<false, true, false, I>
-              : step_buffered_kernel<false, false, false, I>;
+    return t2 ? step_buffered_kernel<false, true, false, I, false>
+              : step_buffered_kernel<false, false, false, I, false>;
   if (two)
-    return t2 ? step_buffered_kernel<true, true, true, I>
-              : step_buffered_kernel<true, false, true, I>;
-  return t2 ? step_buffered_kernel<true, true, false, I>
-            : step_buffered_kernel<true, false, false, I>;
+    return t2 ? step_buffered_kernel<true, true, true, I, false>
+              : step_buffered_kernel<true, false, true, I, false>;
+  return t2 ? step_buffered_kernel<true, true, false, I, false>
+            : step_buffered_kernel<true, false, false, I, false>;
 }
 
+// Synchronous generation with float fitness (after the explicit a1 + a2
+// kernels): one warp per island, IPW islands per warp, every genome's
+// counter equal to G.
+template <bool TRACKED, bool TWO, int IPW>
+__global__ void __launch_bounds__(kResidentThreads)
+    step_float_kernel(RunParams p, uint32_t G, const uint32_t *__restrict__ tin,
+                      const uint64_t *__restrict__ sin, uint32_t *__restrict__ tout,
+                      uint64_t *__restrict__ sout) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint32_t first = warp * IPW;
+  if (first >= p.islands) return;
+  const uint32_t n = p.n;
+  uint32_t t[IPW], T[IPW];
+  uint64_t s[IPW];
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    const uint32_t isl = first + k;
+    t[k] = 0;
+    s[k] = 0;
+    T[k] = G;
+    if (isl < p.islands && lane < n) {
+      t[k] = tin[isl * n + lane];
+      if constexpr (TRACKED) s[k] = sin[isl * n + lane];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    const uint32_t isl = first + k;
+    if (isl >= p.islands) break;
+    counter_step<TRACKED, false, TWO, true>(p, lane, isl, G, t[k], s[k], T[k]);
+    if (lane < n) {
+      tout[isl * n + lane] = t[k];
+      if constexpr (TRACKED) sout[isl * n + lane] = s[k];
+    }
+  }
+}
+
+constexpr int kFloatIslandsPerWarp = 4;
+
 }  // namespace
+
+cudaError_t launch_step_float(const RunParams &p, uint32_t G, const uint32_t *tin,
+                              const uint64_t *sin, uint32_t *tout, uint64_t *sout,
+                              cudaStream_t stream) {
+  constexpr int I = kFloatIslandsPerWarp;
+  const bool tracked = p.policy != HSGA_NONE, two = p.policy == HSGA_HYBRID;
+  const uint32_t wpb = kResidentThreads / 32;
+  const uint32_t warps = (p.islands + I - 1) / I;
+  const uint32_t blocks = (warps + wpb - 1) / wpb;
+  if (!tracked)
+    step_float_kernel<false, false, I><<<blocks, kResidentThreads, 0, stream>>>(p, G, tin, sin,
+                                                                                tout, sout);
+  else if (two)
+    step_float_kernel<true, true, I><<<blocks, kResidentThreads, 0, stream>>>(p, G, tin, sin,
+                                                                              tout, sout);
+  else
+    step_float_kernel<true, false, I><<<blocks, kResidentThreads, 0, stream>>>(p, G, tin, sin,
+                                                                               tout, sout);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t *t,
                                  uint64_t *s, uint32_t *T, uint64_t *mail, uint32_t *ack,
                                  uint4 *inbuf, uint4 *chst, uint32_t *log, uint32_t log_G0,
                                  uint32_t log_gens, cudaStream_t stream) {
   BufferedFn fn =
-      pick_buffered(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID);
+      pick_buffered(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
   const uint32_t wpb = kResidentThreads / 32;
   const uint32_t warps = (p.islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
   const uint32_t blocks = (warps + wpb - 1) / wpb;
@@ -449,7 +527,8 @@ cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, ui
                               uint64_t *s, uint32_t *T, uint64_t *rec, uint32_t *seen,
                               uint32_t *log, uint32_t log_G0, uint32_t log_gens,
                               cudaStream_t stream) {
-  AsyncFn fn = pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID);
+  AsyncFn fn =
+      pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
   const uint32_t wpb = kResidentThreads / 32;
   const uint32_t warps = (p.islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
   const uint32_t blocks = (warps + wpb - 1) / wpb;

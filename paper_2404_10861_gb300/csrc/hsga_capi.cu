@@ -1,6 +1,7 @@
 // hsga_capi.cu -- C-ABI runtime: grid lifetime, device memory, dispatch of
 // the generation kernels, checkpointing, and the host-side site / lookup
 // functions.  Declarations and contracts: include/hsga.h.
+#include <cmath>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -127,6 +128,14 @@ int validate(const hsga_config *c) {
   if (!(c->p_deleterious >= 0.0 && c->p_deleterious <= 1.0)) return HSGA_ERR_INVALID_ARG;
   if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
   if (c->kernel > HSGA_KERNEL_RESIDENT_GRID || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
+  if (c->fitness > HSGA_FITNESS_FLOAT) return HSGA_ERR_INVALID_ARG;
+  if (c->fitness == HSGA_FITNESS_FLOAT) {
+    if (!(c->mutation_sigma > 0.0 && c->mutation_sigma < 1e30)) return HSGA_ERR_INVALID_ARG;
+    if (c->agents_per_island > 32) return HSGA_ERR_INVALID_ARG;
+    if (c->migration_mode == HSGA_MIGRATION_SYNC && c->kernel != HSGA_KERNEL_AUTO &&
+        c->kernel != HSGA_KERNEL_STREAMED)
+      return HSGA_ERR_UNSUPPORTED;
+  }
   if (c->migration_mode > HSGA_MIGRATION_BUFFERED) return HSGA_ERR_INVALID_ARG;
   if (c->migration_mode != HSGA_MIGRATION_SYNC &&
       (c->agents_per_island > 32 || c->deposit_interval > 1))
@@ -162,6 +171,8 @@ RunParams make_params(const hsga_config *c) {
   p.bd_all = thr_bd >= (1ull << 32) ? 1u : 0u;
   p.has_del = thr_bd > thr_ben ? 1u : 0u;
   p.vmask = (1ull << p.bits) - 1;
+  p.flt = c->fitness == HSGA_FITNESS_FLOAT ? 1u : 0u;
+  p.gscale = p.flt ? (float)(c->mutation_sigma / sqrt(24.0 + 1.0 / 12.0) / 16777216.0) : 0.0f;
   p.cols_div = make_fastdiv(p.cols);
   set_round_keys(p);
   return p;
@@ -335,7 +346,7 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
     return HSGA_ERR_CUDA;
   }
   g->resident = false;
-  if (cfg->kernel != HSGA_KERNEL_STREAMED && !g->async) {
+  if (cfg->kernel != HSGA_KERNEL_STREAMED && !g->async && !g->p.flt) {
     g->resident = resident_plan(g->p, &g->plan, cfg->kernel == HSGA_KERNEL_RESIDENT_GRID);
     if (!g->resident && cfg->kernel >= HSGA_KERNEL_RESIDENT) {
       free_grid(g);
@@ -476,6 +487,21 @@ int advance(hsga_grid *g, uint64_t n) {
                                g->rec, g->flags, g->err, g->stream);
       g->launches++;
       done += m;
+    }
+  } else if (g->p.flt) {
+    // float fitness, synchronous: explicit a1 + a2, then one warp per island
+    for (uint64_t k = 0; k < n && e == cudaSuccess; ++k) {
+      const uint64_t G = g->G + k;
+      if (migrates(g->p, G) && !(g->premigrated && k == 0)) {
+        e = launch_migrate(g->p, (uint32_t)G, g->trait[g->cur], g->surf[g->cur], g->rec,
+                           g->stream);
+        g->launches += 2;
+      }
+      if (e == cudaSuccess)
+        e = launch_step_float(g->p, (uint32_t)G, g->trait[g->cur], g->surf[g->cur],
+                              g->trait[1 - g->cur], g->surf[1 - g->cur], g->stream);
+      g->cur = 1 - g->cur;
+      g->launches++;
     }
   } else {
     for (uint64_t k = 0; k < n && e == cudaSuccess; ++k) {

@@ -22,6 +22,7 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 constexpr uint32_t kPurposeMigration = 0;  // with kSlot* in word 0
 constexpr uint32_t kPurposeReplicate = 1;  // first tournament block
 constexpr uint32_t kPurposeSampleDraw = 3; // with island word 0xFFFFFFFF
+constexpr uint32_t kPurposeGauss = 256;    // float fitness: mutation amount
 constexpr uint32_t kSlotEmigrant = 0xFFFFFFFFu;
 constexpr uint32_t kSlotImmigrant = 0xFFFFFFFEu;
 constexpr uint32_t kSlotSample = 0xFFFFFFFDu;
@@ -168,6 +169,8 @@ struct RunParams {
   uint32_t bd32, bd_all;    // deleterious: otherwise w2 < floor(p_ben 2^32) + floor(p_del 2^32)
   uint32_t has_del;         // floor(p_del 2^32) > 0
   uint64_t vmask;          // (1 << bits) - 1
+  uint32_t flt;            // binary32 fitness with Gaussian mutation amounts
+  float gscale;            // float(sigma / sqrt(24 + 1/12) / 2^24)
   FastDiv cols_div;        // island -> (row, column)
   uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (W0, W1)
 };
@@ -341,6 +344,34 @@ __device__ __forceinline__ uint32_t mutate(const RunParams &p, uint32_t trait, u
   const uint32_t bd = (uint32_t)(w2 < p.bd32) | p.bd_all;
   const uint32_t dec = bd & (ben ^ 1u) & (uint32_t)(trait != 0u);
   return trait + inc - dec;
+}
+
+// Float fitness (hsga.h, HSGA_FITNESS_FLOAT): a later candidate wins only if
+// strictly fitter as a binary32 value.
+template <bool FLT>
+__device__ __forceinline__ bool fitter(uint32_t a, uint32_t b) {
+  if constexpr (FLT) return __uint_as_float(a) > __uint_as_float(b);
+  return a > b;
+}
+
+// Sign-restricted Gaussian mutation of a binary32 fitness: the amount is
+// |float(g) * gscale| with g = (B - 48) 2^24 + (q3 >> 8) - 2^23, B the
+// popcount of q0..q2 (Binomial(96, 1/2)) and (q0..q3) = Philox(key; j, island,
+// G, kPurposeGauss): the de Moivre-Laplace approximation to a normal of
+// variance 24 + 1/12, smoothed by a 24-bit uniform.  The round-to-nearest
+// intrinsics keep every float step a single correctly rounded operation.
+__device__ __forceinline__ uint32_t mutate_float(const RunParams &p, uint32_t trait,
+                                                 uint32_t w2, uint32_t j, uint32_t isl,
+                                                 uint32_t G) {
+  const bool ben = (w2 < p.ben32) || p.ben_all;
+  const bool del = !ben && ((w2 < p.bd32) || p.bd_all);
+  if (!ben && !del) return trait;
+  const Words4 q = philox_rk(p, j, isl, G, kPurposeGauss);
+  const int B = __popc(q.x) + __popc(q.y) + __popc(q.z);
+  const int g = (B - 48) * (1 << 24) + (int)(q.w >> 8) - (1 << 23);
+  const float amount = fabsf(__fmul_rn(__int2float_rn(g), p.gscale));
+  const float f = __uint_as_float(trait);
+  return __float_as_uint(ben ? __fadd_rn(f, amount) : __fsub_rn(f, amount));
 }
 
 // Device error word values (first error wins).

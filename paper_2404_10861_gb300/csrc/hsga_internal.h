@@ -48,6 +48,9 @@ cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint
                           const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
                           uint32_t *scratch, cudaStream_t stream, const uint32_t *T = nullptr);
 
+cudaError_t launch_step_float(const RunParams &p, uint32_t G, const uint32_t *tin,
+                              const uint64_t *sin, uint32_t *tout, uint64_t *sout,
+                              cudaStream_t stream);
 cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t *t,
                                  uint64_t *s, uint32_t *T, uint64_t *mail, uint32_t *ack,
                                  uint4 *inbuf, uint4 *chst, uint32_t *log, uint32_t log_G0,

@@ -66,9 +66,16 @@ def test_config_validation_needs_no_gpu(hb):
     bad = [dict(rows=0), dict(n=0), dict(n=65), dict(tournament=0), dict(bits=3),
            dict(policy=7), dict(policy="tilted", W=3), dict(policy="tilted", bits=8, W=8), dict(policy="stretched", W=0),
            dict(p_ben=0.7, p_del=0.5), dict(p_ben=-0.1), dict(kernel=9),
-           dict(policy="hybrid", bits=8, W=4), dict(policy=6)]
+           dict(policy="hybrid", bits=8, W=4), dict(policy=6),
+           dict(fitness="float", sigma=0.0), dict(fitness="float", sigma=-1.0),
+           dict(fitness="float", sigma=1.0, n=33), dict(mode="buffered", n=33),
+           dict(mode="buffered", coarsen=2)]
     for kw in bad:
         cfg = hb.make_config(**kw)
         out = ctypes.c_void_p()
         assert hb.lib().hsga_init_grid(ctypes.byref(cfg), None, ctypes.byref(out)) == -1, kw
     assert hb.lib().hsga_lookup(0, 12, 2, 5, None) == -1
+    cfg = hb.make_config(fitness="float", sigma=1.0)
+    cfg.fitness = 2                                        # not a fitness model
+    out = ctypes.c_void_p()
+    assert hb.lib().hsga_init_grid(ctypes.byref(cfg), None, ctypes.byref(out)) == -1
