@@ -17,6 +17,11 @@ agglomerative-trie algorithm lives in another paper):
   (time, value); the root sits at time -1 and leaves at time T;
 * unifurcations are collapsed; branch lengths are differences in time.
 
+Genomes of free-running runs carry their own deposition counts, so their
+retained times differ; for those, two genomes are compared on the times both
+retain (ascending), and the last match before the first mismatch bounds
+their common ancestry as before (the pairwise form of the same method).
+
 Phylometrics (the on-hardware trial compares sum branch length and mean
 evolutionary distinctiveness between purifying-only and adaptive treatments):
 
@@ -81,6 +86,60 @@ def retained_order(policy: int, S: int, W: int, T: int, coarsen: int = 1):
     sites = np.nonzero(times >= 0)[0]
     order = sites[np.argsort(times[sites], kind="stable")]
     return order, times[order]
+
+
+def retained_times(policy: int, S: int, W: int, T: int, coarsen: int = 1) -> np.ndarray:
+    """Per site, the generation whose differentia it holds after T
+    generations (-1 if empty)."""
+    key = (policy, S, W, T, coarsen)
+    if key not in _RETAINED:
+        k = max(1, coarsen)
+        times = lookup(policy, S, W, -(-T // k)) * k
+        times[times < 0] = -1
+        if len(_RETAINED) > 4096:
+            _RETAINED.clear()
+        _RETAINED[key] = times
+    return _RETAINED[key].copy()
+
+
+_RETAINED: dict = {}
+
+
+def mrca_bounds_mixed(sa: int, Ta: int, sb: int, Tb: int, policy: int, bits: int, W: int,
+                      coarsen: int = 1):
+    """Two surfaces with their own generation counts: (t_prev, t_star) over
+    the generations both still retain, in ascending order -- t_star the first
+    at which their differentiae differ (None if none does), t_prev the last
+    common retained generation before it (-1 if none).  Common ancestry ends
+    at or before t_star."""
+    S = 64 // bits
+    d = differentiae(np.array([sa, sb], dtype=np.uint64), bits)
+    va = {int(t): int(d[0, i]) for i, t in enumerate(retained_times(policy, S, W, Ta, coarsen))
+          if t >= 0}
+    vb = {int(t): int(d[1, i]) for i, t in enumerate(retained_times(policy, S, W, Tb, coarsen))
+          if t >= 0}
+    prev = -1
+    for t in sorted(set(va) & set(vb)):
+        if va[t] != vb[t]:
+            return prev, t
+        prev = t
+    return prev, None
+
+
+def mean_pairwise_distance_mixed(surf, T, policy: int, bits: int, W: int, pairs: int,
+                                 rng, coarsen: int = 1) -> float:
+    """Mean over `pairs` random pairs of (Ta - m) + (Tb - m), m = t_prev of
+    mrca_bounds_mixed: the path length through the estimated common
+    ancestor, as in the trie (whose branching node sits at t_prev)."""
+    surf = np.asarray(surf, dtype=np.uint64)
+    T = np.asarray(T, dtype=np.int64)
+    total = 0
+    for _ in range(pairs):
+        a, b = rng.choice(len(surf), size=2, replace=False)
+        m, _ = mrca_bounds_mixed(int(surf[a]), int(T[a]), int(surf[b]), int(T[b]), policy,
+                                 bits, W, coarsen)
+        total += int(T[a]) + int(T[b]) - 2 * m
+    return total / pairs
 
 
 def mrca_bounds(da: np.ndarray, db: np.ndarray, times: np.ndarray):

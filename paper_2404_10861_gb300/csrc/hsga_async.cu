@@ -95,132 +95,6 @@ __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, 
   T = Tp + 1u;
 }
 
-// IPW islands per warp: lane 4k + j writes word j of island k's record, and
-// lane 4k + d reads the record of island k's neighbour in direction d.
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
-__global__ void __launch_bounds__(kResidentThreads)
-    step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
-                      uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
-                      uint64_t *__restrict__ rec, uint32_t *__restrict__ seen_io, uint32_t *__restrict__ log,
-                      uint32_t log_G0, uint32_t log_gens) {
-  static_assert(4 * IPW <= 32, "one lane per island and record word or direction");
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const uint32_t first = warp * IPW;
-  if (first >= p.islands) return;  // whole warps only; no block barriers are used
-  const uint32_t n = p.n;
-  uint32_t isl[IPW];
-  bool live[IPW];
-  uint32_t pt[IPW][1], pT[IPW][1];
-  uint64_t ps[IPW][1];
-#pragma unroll
-  for (int k = 0; k < IPW; ++k) {
-    isl[k] = first + k;
-    live[k] = isl[k] < p.islands;
-    pt[k][0] = pT[k][0] = 0;
-    ps[k][0] = 0;
-    if (live[k] && lane < n) {
-      pt[k][0] = tplane[isl[k] * n + lane];
-      if constexpr (TRACKED) ps[k][0] = splane[isl[k] * n + lane];
-      pT[k][0] = Tplane[isl[k] * n + lane];
-    }
-  }
-  // reader lane r = 4k + d: island k, direction d
-  const uint32_t rk = lane >> 2, rd = lane & 3u;
-  const bool reader = lane < 4u * IPW && first + rk < p.islands;
-  const uint32_t risl = first + rk;
-  uint32_t seen = reader ? seen_io[risl * 4 + rd] : 0u;
-  const uint32_t rnb = reader ? neighbour(p, risl, rd) : 0u;
-  // block lane b: b < IPW the emigrant block of island b, IPW <= b < 2 IPW
-  // the placement block of island b - IPW
-  const uint32_t bk = lane < (uint32_t)IPW ? lane : (lane < 2u * IPW ? lane - IPW : 0u);
-  for (uint32_t g = 0; g < ngen; ++g) {
-    const uint32_t G = G0 + g;
-    const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
-    if (migrates(p, G)) {
-      const Words4 m = philox_rk(p, lane >= (uint32_t)IPW ? kSlotImmigrant : kSlotEmigrant,
-                                 first + bk, G, kPurposeMigration);
-      // a1: lane 4k + j gathers word j of island k's emigrant and publishes it
-      uint32_t word = 0, dir = 0;
-#pragma unroll
-      for (int k = 0; k < IPW; ++k) {
-        const uint32_t eslot = uindex(__shfl_sync(kFull, m.x, k), n);
-        const uint32_t dk = __shfl_sync(kFull, m.y, k) >> 30;
-        const uint32_t vt = __shfl_sync(kFull, pt[k][0], eslot);
-        const uint64_t vs = shfl64(ps[k][0], eslot);
-        const uint32_t vT = __shfl_sync(kFull, pT[k][0], eslot);
-        if (rk == (uint32_t)k) {
-          word = rd == 0 ? vt : rd == 1 ? (uint32_t)vs : rd == 2 ? (uint32_t)(vs >> 32) : vT;
-          dir = dk;
-        }
-      }
-      if (reader) {
-        const uint32_t st = ((G + 1u) << 3) | (dir << 1);
-        st_relaxed_u64(rec + 4 * (size_t)risl + rd, ((uint64_t)st << 32) | word);
-      }
-      // a2: each reader lane looks at its neighbour's latest record
-      bool take = false;
-      uint32_t s1 = 0, r[4] = {0, 0, 0, 0};
-      if (reader) {
-        uint64_t v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = ld_relaxed_u64(rec + 4 * (size_t)rnb + j);
-        s1 = (uint32_t)(v[0] >> 32);
-        const bool whole = (uint32_t)(v[1] >> 32) == s1 && (uint32_t)(v[2] >> 32) == s1 &&
-                           (uint32_t)(v[3] >> 32) == s1;
-        if (whole && (s1 >> 3) > seen) {
-          seen = s1 >> 3;
-          take = ((s1 >> 1) & 3u) == ((rd + 2u) & 3u);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) r[j] = (uint32_t)v[j];
-      }
-      if (reader && logging)
-        log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = take ? (s1 >> 3) : 0u;
-      const uint32_t it = r[0], iT = r[3];
-      const uint64_t is = ((uint64_t)r[2] << 32) | r[1];
-      const uint32_t arrivals = __ballot_sync(kFull, take);
-      const uint32_t place[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-      for (int k = 0; k < IPW; ++k) {
-        const uint32_t bits = (arrivals >> (4 * k)) & 0xFu;
-        if (!bits) continue;
-#pragma unroll
-        for (uint32_t dd = 0; dd < 4; ++dd) {
-          if (bits & (1u << dd)) {
-            const uint32_t slot = uindex(__shfl_sync(kFull, place[dd], IPW + k), n);
-            const uint32_t src = 4u * k + dd;
-            const uint32_t vt = __shfl_sync(kFull, it, src);
-            const uint64_t vs = shfl64(is, src);
-            const uint32_t vT = __shfl_sync(kFull, iT, src);
-            if (lane == slot) {
-              pt[k][0] = vt;
-              ps[k][0] = vs;
-              pT[k][0] = vT;
-            }
-          }
-        }
-      }
-    } else if (reader && logging) {
-      log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = 0;
-    }
-    // a3-a6 for every owned island, with per-genome counters
-#pragma unroll
-    for (int k = 0; k < IPW; ++k)
-      if (live[k])
-        counter_step<TRACKED, T2, TWO, FLT>(p, lane, isl[k], G, pt[k][0], ps[k][0], pT[k][0]);
-  }
-#pragma unroll
-  for (int k = 0; k < IPW; ++k) {
-    if (live[k] && lane < n) {
-      tplane[isl[k] * n + lane] = pt[k][0];
-      if constexpr (TRACKED) splane[isl[k] * n + lane] = ps[k][0];
-      Tplane[isl[k] * n + lane] = pT[k][0];
-    }
-  }
-  if (reader) seen_io[risl * 4 + rd] = seen;
-}
-
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -236,9 +110,198 @@ __device__ __forceinline__ uint32_t pick4(uint32_t a, uint32_t b, uint32_t c, ui
   return i == 0 ? a : i == 1 ? b : i == 2 ? c : d;
 }
 
-// Buffered free-running migration: the paper's per-neighbour buffers (one
-// genome to send, four received) with completion flags.  Lane 4k + d of a
-// warp serves island first + k in direction d.  Each migrating generation it
+// ------------------------------------------------------------- octets ---
+// A warp serves IPW consecutive islands (an "octet") at a time: lane j holds
+// agent j of each island, and lane 4k + d serves island k in direction d for
+// migration.  A launch keeps every warp resident and gives each a strided
+// set of octets; each generation a warp advances all of its octets by one
+// generation, so the whole grid progresses together (as the paper's
+// processing elements do) however many islands there are.  A warp with a
+// single octet keeps it in registers for the whole launch; otherwise octets
+// are loaded and stored in place every generation.
+template <int IPW>
+struct Octet {
+  uint32_t first;
+  bool live[IPW];
+  uint32_t t[IPW], T[IPW];
+  uint64_t s[IPW];
+};
+
+template <bool TRACKED, int IPW>
+__device__ __forceinline__ void load_octet(const RunParams &p, Octet<IPW> &o, uint32_t first,
+                                           uint32_t lane, const uint32_t *tplane,
+                                           const uint64_t *splane, const uint32_t *Tplane) {
+  o.first = first;
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    const uint32_t isl = first + k;
+    o.live[k] = isl < p.islands;
+    o.t[k] = o.T[k] = 0;
+    o.s[k] = 0;
+    if (o.live[k] && lane < p.n) {
+      o.t[k] = tplane[isl * p.n + lane];
+      if constexpr (TRACKED) o.s[k] = splane[isl * p.n + lane];
+      o.T[k] = Tplane[isl * p.n + lane];
+    }
+  }
+}
+
+template <bool TRACKED, int IPW>
+__device__ __forceinline__ void store_octet(const RunParams &p, const Octet<IPW> &o,
+                                            uint32_t lane, uint32_t *tplane, uint64_t *splane,
+                                            uint32_t *Tplane) {
+#pragma unroll
+  for (int k = 0; k < IPW; ++k) {
+    const uint32_t isl = o.first + k;
+    if (o.live[k] && lane < p.n) {
+      tplane[isl * p.n + lane] = o.t[k];
+      if constexpr (TRACKED) splane[isl * p.n + lane] = o.s[k];
+      Tplane[isl * p.n + lane] = o.T[k];
+    }
+  }
+}
+
+// a3-a6 for every island of the octet
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+__device__ __forceinline__ void octet_step(const RunParams &p, Octet<IPW> &o, uint32_t lane,
+                                           uint32_t G) {
+#pragma unroll
+  for (int k = 0; k < IPW; ++k)
+    if (o.live[k])
+      counter_step<TRACKED, T2, TWO, FLT>(p, lane, o.first + k, G, o.t[k], o.s[k], o.T[k]);
+}
+
+// Octets owned by this warp: warp, warp + nwarps, ...
+__device__ __forceinline__ uint32_t owned_octets(uint32_t warp, uint32_t nwarps,
+                                                 uint32_t octets) {
+  return warp < octets ? (octets - warp + nwarps - 1) / nwarps : 0u;
+}
+
+// ------------------------------------------------- latest-emigrant mode ---
+// One generation of one octet: lane 4k + j publishes word j of island k's
+// emigrant record, and lane 4k + d reads the record of island k's neighbour
+// in direction d (`seen`: the newest stamp it has seen from it).
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+__device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> &o,
+                                                 uint32_t &seen, uint32_t lane, uint32_t G,
+                                                 uint64_t *rec, uint32_t *log,
+                                                 uint32_t log_G0, uint32_t log_gens) {
+  const uint32_t n = p.n, first = o.first;
+  const uint32_t rk = lane >> 2, rd = lane & 3u;
+  const bool reader = lane < 4u * IPW && first + rk < p.islands;
+  const uint32_t risl = first + rk;
+  const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
+  if (migrates(p, G)) {
+    // block lane b: b < IPW the emigrant block of island b, IPW <= b < 2 IPW
+    // the placement block of island b - IPW
+    const uint32_t bk = lane < (uint32_t)IPW ? lane : (lane < 2u * IPW ? lane - IPW : 0u);
+    const Words4 m = philox_rk(p, lane >= (uint32_t)IPW ? kSlotImmigrant : kSlotEmigrant,
+                               first + bk, G, kPurposeMigration);
+    // a1: lane 4k + j gathers word j of island k's emigrant and publishes it
+    uint32_t word = 0, dir = 0;
+#pragma unroll
+    for (int k = 0; k < IPW; ++k) {
+      const uint32_t eslot = uindex(__shfl_sync(kFull, m.x, k), n);
+      const uint32_t dk = __shfl_sync(kFull, m.y, k) >> 30;
+      const uint32_t vt = __shfl_sync(kFull, o.t[k], eslot);
+      const uint64_t vs = shfl64(o.s[k], eslot);
+      const uint32_t vT = __shfl_sync(kFull, o.T[k], eslot);
+      if (rk == (uint32_t)k) {
+        word = pick4(vt, (uint32_t)vs, (uint32_t)(vs >> 32), vT, rd);
+        dir = dk;
+      }
+    }
+    if (reader) {
+      const uint32_t st = ((G + 1u) << 3) | (dir << 1);
+      st_relaxed_u64(rec + 4 * (size_t)risl + rd, ((uint64_t)st << 32) | word);
+    }
+    // a2: each reader lane looks at its neighbour's latest record
+    bool take = false;
+    uint32_t s1 = 0, r[4] = {0, 0, 0, 0};
+    if (reader) {
+      const uint32_t rnb = neighbour(p, risl, rd);
+      uint64_t v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = ld_relaxed_u64(rec + 4 * (size_t)rnb + j);
+      s1 = (uint32_t)(v[0] >> 32);
+      const bool whole = (uint32_t)(v[1] >> 32) == s1 && (uint32_t)(v[2] >> 32) == s1 &&
+                         (uint32_t)(v[3] >> 32) == s1;
+      if (whole && (s1 >> 3) > seen) {
+        seen = s1 >> 3;
+        take = ((s1 >> 1) & 3u) == ((rd + 2u) & 3u);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) r[j] = (uint32_t)v[j];
+    }
+    if (reader && logging)
+      log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = take ? (s1 >> 3) : 0u;
+    const uint64_t is = ((uint64_t)r[2] << 32) | r[1];
+    const uint32_t arrivals = __ballot_sync(kFull, take);
+#pragma unroll
+    for (int k = 0; k < IPW; ++k) {
+      const uint32_t bits = (arrivals >> (4 * k)) & 0xFu;
+      if (!bits) continue;
+#pragma unroll
+      for (uint32_t dd = 0; dd < 4; ++dd) {
+        if (bits & (1u << dd)) {
+          const uint32_t slot =
+              uindex(__shfl_sync(kFull, pick4(m.x, m.y, m.z, m.w, dd), IPW + k), n);
+          const uint32_t src = 4u * k + dd;
+          const uint32_t vt = __shfl_sync(kFull, r[0], src);
+          const uint64_t vs = shfl64(is, src);
+          const uint32_t vT = __shfl_sync(kFull, r[3], src);
+          if (lane == slot) {
+            o.t[k] = vt;
+            o.s[k] = vs;
+            o.T[k] = vT;
+          }
+        }
+      }
+    }
+  } else if (reader && logging) {
+    log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = 0;
+  }
+  octet_step<TRACKED, T2, TWO, IPW, FLT>(p, o, lane, G);
+}
+
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+__global__ void __launch_bounds__(kResidentThreads)
+    step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
+                      uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
+                      uint64_t *__restrict__ rec, uint32_t *__restrict__ seen_io,
+                      uint32_t *__restrict__ log, uint32_t log_G0, uint32_t log_gens) {
+  static_assert(4 * IPW <= 32, "one lane per island and record word or direction");
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t octets = (p.islands + IPW - 1) / IPW;
+  const uint32_t owned = owned_octets(warp, nwarps, octets);
+  if (owned == 0) return;  // whole warps only; no block barriers are used
+  const uint32_t rk = lane >> 2, rd = lane & 3u;
+  Octet<IPW> o;
+  uint32_t seen = 0;
+  for (uint32_t g = 0; g < ngen; ++g) {
+    for (uint32_t j = 0; j < owned; ++j) {
+      const uint32_t first = (warp + j * nwarps) * IPW;
+      const bool reader = lane < 4u * IPW && first + rk < p.islands;
+      if (owned > 1 || g == 0) {
+        load_octet<TRACKED>(p, o, first, lane, tplane, splane, Tplane);
+        seen = reader ? seen_io[(first + rk) * 4 + rd] : 0u;
+      }
+      async_generation<TRACKED, T2, TWO, IPW, FLT>(p, o, seen, lane, G0 + g, rec, log, log_G0,
+                                                   log_gens);
+      if (owned > 1 || g + 1 == ngen) {
+        store_octet<TRACKED>(p, o, lane, tplane, splane, Tplane);
+        if (reader) seen_io[(first + rk) * 4 + rd] = seen;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------- per-neighbour buffers ---
+// The paper's per-neighbour buffers (one genome to send, four received)
+// with completion flags.  Lane 4k + d serves island k of the octet in
+// direction d.  Each migrating generation it
 //   receive: takes the genome on the channel from that neighbour if it is the
 //            next post (post numbers count from 1 per channel), appends it to
 //            its receive buffer and acknowledges it;
@@ -252,9 +315,126 @@ __device__ __forceinline__ uint32_t pick4(uint32_t a, uint32_t b, uint32_t c, ui
 // genome word under the post number: a 64-bit relaxed access is single-copy
 // atomic, so a reader that sees the expected post number in all four words
 // holds the whole genome, and a sender rewrites the channel only after its
-// receiver acknowledged the previous post.  No waits, no fences.  The lane
-// state {posts, taken, waiting} and the first three buffered genomes persist
-// in global memory between launches; the fourth is placed as it arrives.
+// receiver acknowledged the previous post.  No waits, no fences; within a
+// generation every channel store follows a warp vote on every channel load.  The lane
+// state {posts, taken, waiting} and the first three buffered genomes live in
+// global memory between octet visits; the fourth is placed as it arrives.
+struct LaneChannel {
+  uint32_t posts, taken, waiting;
+};
+
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+__device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IPW> &o,
+                                                    LaneChannel &ch, uint32_t lane, uint32_t G,
+                                                    uint64_t *mail, uint32_t *ack,
+                                                    uint4 *inbuf, uint32_t *log,
+                                                    uint32_t log_G0, uint32_t log_gens) {
+  const uint32_t n = p.n;
+  const uint32_t rk = lane >> 2, rd = lane & 3u;
+  const uint32_t me = o.first + rk;
+  const bool mine = lane < 4u * IPW && me < p.islands;
+  const size_t c = 4 * (size_t)me + rd;  // own channel toward d, own receive buffer from d
+  const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
+  uint32_t entry = 0;
+  if (migrates(p, G)) {
+    const size_t inc = mine ? 4 * (size_t)neighbour(p, me, rd) + ((rd + 2u) & 3u) : 0;
+    uint64_t v[4] = {0, 0, 0, 0};
+    uint32_t a = 0;
+    if (mine) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = ld_relaxed_u64(mail + 4 * inc + j);
+      a = ld_relaxed_u32(ack + c);
+    }
+    // receive.  The warp votes on every word it loaded (the acknowledgement
+    // never exceeds the posts, so that term only ties the vote to it) before
+    // any lane writes a channel or an acknowledgement: each island
+    // generation then reads before it writes, which is what makes the logged
+    // exchanges causally ordered.
+    const uint32_t seq = (uint32_t)(v[0] >> 32);
+    const bool take = mine && seq == ch.taken + 1u && (uint32_t)(v[1] >> 32) == seq &&
+                      (uint32_t)(v[2] >> 32) == seq && (uint32_t)(v[3] >> 32) == seq &&
+                      a <= ch.posts;
+    const uint32_t takes = __ballot_sync(kFull, take);
+    const uint32_t sends = __ballot_sync(kFull, mine && a == ch.posts);
+    const bool got = (takes >> lane) & 1u;
+    const uint4 arrived =
+        make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2], (uint32_t)v[3]);
+    if (got) {
+      if (ch.waiting < 3u) inbuf[4 * c + ch.waiting] = arrived;
+      ++ch.waiting;
+      ch.taken = seq;
+      st_relaxed_u32(ack + inc, seq);
+      entry = seq << 1;
+    }
+    // place full buffers (a buffer fills only as its fourth genome arrives)
+    const uint32_t full = __ballot_sync(kFull, mine && ch.waiting == 4u);
+    if (full) {
+      Words4 pv{0, 0, 0, 0};
+      uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
+      if (mine && ch.waiting == 4u) {
+        pv = philox_rk(p, kSlotImmigrant, me, G, 1u + rd);
+        b0 = inbuf[4 * c];
+        b1 = inbuf[4 * c + 1];
+        b2 = inbuf[4 * c + 2];
+        ch.waiting = 0;
+      }
+#pragma unroll
+      for (int k = 0; k < IPW; ++k) {
+        uint32_t bits = (full >> (4 * k)) & 0xFu;
+        while (bits) {
+          const uint32_t src = 4u * k + (uint32_t)(__ffs(bits) - 1);
+          bits &= bits - 1u;
+#pragma unroll
+          for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t slot =
+                uindex(__shfl_sync(kFull, pick4(pv.x, pv.y, pv.z, pv.w, j), src), n);
+            const uint4 bj = j == 0 ? b0 : j == 1 ? b1 : j == 2 ? b2 : arrived;
+            const uint32_t gt = __shfl_sync(kFull, bj.x, src);
+            const uint32_t glo = __shfl_sync(kFull, bj.y, src);
+            const uint32_t ghi = __shfl_sync(kFull, bj.z, src);
+            const uint32_t gT = __shfl_sync(kFull, bj.w, src);
+            if (lane == slot) {
+              o.t[k] = gt;
+              o.s[k] = ((uint64_t)ghi << 32) | glo;
+              o.T[k] = gT;
+            }
+          }
+        }
+      }
+    }
+    // send on every channel whose previous post was acknowledged
+    const bool send = (sends >> lane) & 1u;
+    if (sends) {
+      const Words4 w = philox_rk(p, kSlotEmigrant, me, G, kPurposeMigration);
+      const uint32_t slot = uindex(pick4(w.x, w.y, w.z, w.w, rd), n);
+      uint32_t et = 0, eT = 0;
+      uint64_t es = 0;
+#pragma unroll
+      for (int k = 0; k < IPW; ++k) {
+        const uint32_t vt = __shfl_sync(kFull, o.t[k], slot);
+        const uint64_t vs = shfl64(o.s[k], slot);
+        const uint32_t vT = __shfl_sync(kFull, o.T[k], slot);
+        if (rk == (uint32_t)k) {
+          et = vt;
+          es = vs;
+          eT = vT;
+        }
+      }
+      if (send) {
+        ++ch.posts;
+        const uint64_t stamp = (uint64_t)ch.posts << 32;
+        st_relaxed_u64(mail + 4 * c, stamp | et);
+        st_relaxed_u64(mail + 4 * c + 1, stamp | (uint32_t)es);
+        st_relaxed_u64(mail + 4 * c + 2, stamp | (uint32_t)(es >> 32));
+        st_relaxed_u64(mail + 4 * c + 3, stamp | eT);
+        entry |= 1u;
+      }
+    }
+  }
+  if (mine && logging) log[((size_t)me * log_gens + (G - log_G0)) * 4 + rd] = entry;
+  octet_step<TRACKED, T2, TWO, IPW, FLT>(p, o, lane, G);
+}
+
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
 __global__ void __launch_bounds__(kResidentThreads)
     step_buffered_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
@@ -265,143 +445,33 @@ __global__ void __launch_bounds__(kResidentThreads)
   static_assert(4 * IPW <= 32, "one lane per island and direction");
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const uint32_t first = warp * IPW;
-  if (first >= p.islands) return;  // whole warps only; no block barriers are used
-  const uint32_t n = p.n;
-  bool live[IPW];
-  uint32_t pt[IPW][1], pT[IPW][1];
-  uint64_t ps[IPW][1];
-#pragma unroll
-  for (int k = 0; k < IPW; ++k) {
-    const uint32_t isl = first + k;
-    live[k] = isl < p.islands;
-    pt[k][0] = pT[k][0] = 0;
-    ps[k][0] = 0;
-    if (live[k] && lane < n) {
-      pt[k][0] = tplane[isl * n + lane];
-      if constexpr (TRACKED) ps[k][0] = splane[isl * n + lane];
-      pT[k][0] = Tplane[isl * n + lane];
-    }
-  }
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t octets = (p.islands + IPW - 1) / IPW;
+  const uint32_t owned = owned_octets(warp, nwarps, octets);
+  if (owned == 0) return;  // whole warps only; no block barriers are used
   const uint32_t rk = lane >> 2, rd = lane & 3u;
-  const bool mine = lane < 4u * IPW && first + rk < p.islands;
-  const uint32_t me = first + rk;
-  const size_t c = 4 * (size_t)me + rd;  // own channel toward d, own receive buffer from d
-  const size_t inc = mine ? 4 * (size_t)neighbour(p, me, rd) + ((rd + 2u) & 3u) : 0;
-  uint32_t posts = 0, taken = 0, waiting = 0;
-  if (mine) {
-    const uint4 st = chst[c];
-    posts = st.x;
-    taken = st.y;
-    waiting = st.z;
-  }
+  Octet<IPW> o;
+  LaneChannel ch{0, 0, 0};
   for (uint32_t g = 0; g < ngen; ++g) {
-    const uint32_t G = G0 + g;
-    const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
-    uint32_t entry = 0;
-    if (migrates(p, G)) {
-      uint64_t v[4] = {0, 0, 0, 0};
-      uint32_t a = 0;
-      if (mine) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = ld_relaxed_u64(mail + 4 * inc + j);
-        a = ld_relaxed_u32(ack + c);
-      }
-      // receive
-      const uint32_t seq = (uint32_t)(v[0] >> 32);
-      const bool got = mine && seq == taken + 1u && (uint32_t)(v[1] >> 32) == seq &&
-                       (uint32_t)(v[2] >> 32) == seq && (uint32_t)(v[3] >> 32) == seq;
-      const uint4 arrived = make_uint4((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2],
-                                       (uint32_t)v[3]);
-      if (got) {
-        if (waiting < 3u) inbuf[4 * c + waiting] = arrived;
-        ++waiting;
-        taken = seq;
-        st_relaxed_u32(ack + inc, seq);
-        entry = seq << 1;
-      }
-      // place full buffers (a buffer fills only as its fourth genome arrives)
-      const uint32_t full = __ballot_sync(kFull, mine && waiting == 4u);
-      if (full) {
-        Words4 pv{0, 0, 0, 0};
-        uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
-        if (mine && waiting == 4u) {
-          pv = philox_rk(p, kSlotImmigrant, me, G, 1u + rd);
-          b0 = inbuf[4 * c];
-          b1 = inbuf[4 * c + 1];
-          b2 = inbuf[4 * c + 2];
-          waiting = 0;
-        }
-#pragma unroll
-        for (int k = 0; k < IPW; ++k) {
-          uint32_t bits = (full >> (4 * k)) & 0xFu;
-          while (bits) {
-            const uint32_t src = 4u * k + (uint32_t)(__ffs(bits) - 1);
-            bits &= bits - 1u;
-#pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {
-              const uint32_t slot =
-                  uindex(__shfl_sync(kFull, pick4(pv.x, pv.y, pv.z, pv.w, j), src), n);
-              const uint4 bj = j == 0 ? b0 : j == 1 ? b1 : j == 2 ? b2 : arrived;
-              const uint32_t gt = __shfl_sync(kFull, bj.x, src);
-              const uint32_t glo = __shfl_sync(kFull, bj.y, src);
-              const uint32_t ghi = __shfl_sync(kFull, bj.z, src);
-              const uint32_t gT = __shfl_sync(kFull, bj.w, src);
-              if (lane == slot) {
-                pt[k][0] = gt;
-                ps[k][0] = ((uint64_t)ghi << 32) | glo;
-                pT[k][0] = gT;
-              }
-            }
-          }
+    for (uint32_t j = 0; j < owned; ++j) {
+      const uint32_t first = (warp + j * nwarps) * IPW;
+      const bool mine = lane < 4u * IPW && first + rk < p.islands;
+      const size_t c = 4 * (size_t)(first + rk) + rd;
+      if (owned > 1 || g == 0) {
+        load_octet<TRACKED>(p, o, first, lane, tplane, splane, Tplane);
+        if (mine) {
+          const uint4 st = chst[c];
+          ch = LaneChannel{st.x, st.y, st.z};
         }
       }
-      // send on every channel whose previous post was acknowledged
-      const bool send = mine && a == posts;
-      if (__any_sync(kFull, send)) {
-        const Words4 w = philox_rk(p, kSlotEmigrant, me, G, kPurposeMigration);
-        const uint32_t slot = uindex(pick4(w.x, w.y, w.z, w.w, rd), n);
-        uint32_t et = 0, eT = 0;
-        uint64_t es = 0;
-#pragma unroll
-        for (int k = 0; k < IPW; ++k) {
-          const uint32_t vt = __shfl_sync(kFull, pt[k][0], slot);
-          const uint64_t vs = shfl64(ps[k][0], slot);
-          const uint32_t vT = __shfl_sync(kFull, pT[k][0], slot);
-          if (rk == (uint32_t)k) {
-            et = vt;
-            es = vs;
-            eT = vT;
-          }
-        }
-        if (send) {
-          ++posts;
-          const uint64_t stamp = (uint64_t)posts << 32;
-          st_relaxed_u64(mail + 4 * c, stamp | et);
-          st_relaxed_u64(mail + 4 * c + 1, stamp | (uint32_t)es);
-          st_relaxed_u64(mail + 4 * c + 2, stamp | (uint32_t)(es >> 32));
-          st_relaxed_u64(mail + 4 * c + 3, stamp | eT);
-          entry |= 1u;
-        }
+      buffered_generation<TRACKED, T2, TWO, IPW, FLT>(p, o, ch, lane, G0 + g, mail, ack, inbuf,
+                                                      log, log_G0, log_gens);
+      if (owned > 1 || g + 1 == ngen) {
+        store_octet<TRACKED>(p, o, lane, tplane, splane, Tplane);
+        if (mine) chst[c] = make_uint4(ch.posts, ch.taken, ch.waiting, 0u);
       }
     }
-    if (mine && logging) log[((size_t)me * log_gens + (G - log_G0)) * 4 + rd] = entry;
-    // a3-a6 for every owned island, with per-genome counters
-#pragma unroll
-    for (int k = 0; k < IPW; ++k)
-      if (live[k])
-        counter_step<TRACKED, T2, TWO, FLT>(p, lane, first + k, G, pt[k][0], ps[k][0], pT[k][0]);
   }
-#pragma unroll
-  for (int k = 0; k < IPW; ++k) {
-    const uint32_t isl = first + k;
-    if (live[k] && lane < n) {
-      tplane[isl * n + lane] = pt[k][0];
-      if constexpr (TRACKED) splane[isl * n + lane] = ps[k][0];
-      Tplane[isl * n + lane] = pT[k][0];
-    }
-  }
-  if (mine) chst[c] = make_uint4(posts, taken, waiting, 0u);
 }
 
 constexpr int kAsyncIslandsPerWarp = 8;
@@ -487,6 +557,21 @@ __global__ void __launch_bounds__(kResidentThreads)
 
 constexpr int kFloatIslandsPerWarp = 4;
 
+// Blocks for a free-running launch: one warp per octet, but never more
+// blocks than the device keeps resident at once, so that every island
+// advances in the same pass over the grid (warps then own several octets).
+uint32_t resident_blocks(const void *fn, uint32_t islands) {
+  const uint32_t wpb = kResidentThreads / 32;
+  const uint32_t octets = (islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
+  const uint32_t need = (octets + wpb - 1) / wpb;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResidentThreads, 0);
+  const uint32_t cap = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
+  return need < cap ? need : cap;
+}
+
 }  // namespace
 
 cudaError_t launch_step_float(const RunParams &p, uint32_t G, const uint32_t *tin,
@@ -515,9 +600,7 @@ cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen,
                                  uint32_t log_gens, cudaStream_t stream) {
   BufferedFn fn =
       pick_buffered(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
-  const uint32_t wpb = kResidentThreads / 32;
-  const uint32_t warps = (p.islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
-  const uint32_t blocks = (warps + wpb - 1) / wpb;
+  const uint32_t blocks = resident_blocks((const void *)fn, p.islands);
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, mail, ack, inbuf, chst, log,
                                                log_G0, log_gens);
   return cudaGetLastError();
@@ -529,9 +612,7 @@ cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, ui
                               cudaStream_t stream) {
   AsyncFn fn =
       pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
-  const uint32_t wpb = kResidentThreads / 32;
-  const uint32_t warps = (p.islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
-  const uint32_t blocks = (warps + wpb - 1) / wpb;
+  const uint32_t blocks = resident_blocks((const void *)fn, p.islands);
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, rec, seen, log, log_G0,
                                                log_gens);
   return cudaGetLastError();

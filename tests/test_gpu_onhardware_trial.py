@@ -1,5 +1,5 @@
 """The paper's on-hardware trial ("Results › On-hardware Trial") at its
-array sizes, in integer form, on the GPU: 100x100, 500x500 and 750x750
+array sizes on the GPU: 100x100, 500x500 and 750x750
 islands of 32 agents, tournament size 5, 33% deleterious mutations
 (purifying-only) or the same plus 0.3% beneficial ones (adaption-enabled),
 4 replicates per treatment, one genome sampled per island, reconstruction
@@ -9,6 +9,15 @@ length and greater mean evolutionary distinctiveness.  The runs here are
 shorter than the paper's 1,000,000 generations (GENERATIONS below) so the
 test finishes in minutes; reconstruction and phylometrics use the oracle's
 analysis code.
+
+Three variants: integer fitness with synchronous migration; the paper's
+binary32 fitness with sign-restricted Gaussian mutation amounts (sigma 1),
+synchronous; and binary32 fitness with the WSE's own free-running protocol
+(per-neighbour send and receive buffers).  Free-running genomes carry their
+own generation counters, which spread over hundreds of values (every
+migration hands over an older genome), so that variant reconstructs from up
+to 10,000 genomes drawn from the whole population among those that share the
+most common counter.
 """
 import numpy as np
 import pytest
@@ -33,28 +42,50 @@ def hb():
     return binding
 
 
-def trial(hb, side, adaptive, seed):
+VARIANTS = {"integer": dict(),
+            "float": dict(fitness="float", sigma=1.0),
+            "float-buffered": dict(fitness="float", sigma=1.0, mode="buffered")}
+
+
+def trial(hb, side, adaptive, seed, variant):
     kw = dict(rows=side, cols=side, n=32, tournament=5, policy="tilted", bits=1, W=2,
-              p_ben=0.003 if adaptive else 0.0, p_del=0.33, seed=seed)
+              p_ben=0.003 if adaptive else 0.0, p_del=0.33, seed=seed, **VARIANTS[variant])
     with hb.Grid(**kw) as g:
         g.run(GENERATIONS)
-        words, _ = g.sample(min(10_000, side * side))
-    surf = words[:, 1].astype(np.uint64) | (words[:, 2].astype(np.uint64) << np.uint64(32))
-    tree = phylo.reconstruct(surf, 1, 1, 2, GENERATIONS)
+        if kw.get("mode") == "buffered":
+            _, s = g.population()
+            T = g.counters()
+        else:
+            words, _ = g.sample(min(10_000, side * side))
+    if kw.get("mode") == "buffered":
+        assert int(T.max()) - int(T.min()) > 20            # counters spread
+        Tm = int(np.bincount(T).argmax())
+        pool = np.nonzero(T == Tm)[0]
+        pick = np.random.default_rng(seed).choice(pool, size=min(10_000, len(pool)),
+                                                 replace=False)
+        surf, T_rec = s[pick], Tm
+    else:
+        surf = (words[:, 1].astype(np.uint64)
+                | (words[:, 2].astype(np.uint64) << np.uint64(32)))
+        T_rec = GENERATIONS
+    tree = phylo.reconstruct(surf, 1, 1, 2, T_rec)
     m = phylo.phylometrics(tree)
-    return m["sum_branch_length"], m["mean_evolutionary_distinctiveness"]
+    return m["sum_branch_length"], m["mean_evolutionary_distinctiveness"], len(surf)
 
 
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("side", SIDES)
-def test_purifying_only_has_longer_phylogenies(hb, side):
+def test_purifying_only_has_longer_phylogenies(hb, side, variant):
     res = {True: [], False: []}
     for adaptive in (True, False):
         for r in range(REPLICATES):
-            res[adaptive].append(trial(hb, side, adaptive, seed=7000 + 97 * side + r))
+            res[adaptive].append(trial(hb, side, adaptive, seed=7000 + 97 * side + r,
+                                       variant=variant))
     adapt = np.array(res[True])
     purif = np.array(res[False])
-    print(f"side {side}: sum branch length purifying {purif[:, 0].mean():.0f} vs adaptive "
-          f"{adapt[:, 0].mean():.0f}; mean ED {purif[:, 1].mean():.1f} vs {adapt[:, 1].mean():.1f}")
+    print(f"{variant} side {side}: sum branch length purifying {purif[:, 0].mean():.0f} vs "
+          f"adaptive {adapt[:, 0].mean():.0f}; mean ED {purif[:, 1].mean():.1f} vs "
+          f"{adapt[:, 1].mean():.1f}; genomes {purif[:, 2].mean():.0f} vs {adapt[:, 2].mean():.0f}")
     for k in (0, 1):
         assert purif[:, k].min() > adapt[:, k].max()          # every replicate, as in the paper
         assert stats.mannwhitneyu(purif[:, k], adapt[:, k], alternative="greater").pvalue < 0.05

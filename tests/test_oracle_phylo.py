@@ -159,3 +159,39 @@ def test_adaptive_vs_neutral_separation(orc):
         on = [m[key] for m in res[True]]
         off = [m[key] for m in res[False]]
         assert stats.mannwhitneyu(off, on, alternative="greater").pvalue < 0.05, (key, on, off)
+
+
+def test_mixed_counts_bound_the_true_mrca(orc):
+    # genome a sampled at G1, genome b at G2 > G1 of the same pedigree: every
+    # generation both still retain from before their true common ancestry
+    # must match, so the first mismatch is never earlier than it
+    c = orc.Config(rows=3, cols=3, n=16, tournament=2, policy=orc.TILTED, bits=1, W=2,
+                   interval=1, seed=3)
+    G1, G2 = 700, 1300
+    t1, s1, par1 = orc.run(c, generations=G1, track_parents=True)
+    t2, s2, par2 = orc.run(c, trait=t1, surf=s1, G0=G1, generations=G2 - G1,
+                           track_parents=True)
+    rng = np.random.default_rng(1)
+    hits = 0
+    for _ in range(400):
+        x, y = (int(v) for v in rng.integers(0, c.agents, size=2))
+        z = int(phylo.lineage(par2, y)[0])                 # y's ancestor at G1
+        d_true = G1 if z == x else phylo.true_mrca_generation(par1, x, z)
+        t_prev, t_star = phylo.mrca_bounds_mixed(int(s1[x]), G1, int(s2[y]), G2, c.policy,
+                                                 c.bits, c.W)
+        assert t_star is None or t_star >= d_true
+        hits += t_star is not None
+    assert hits > 30
+
+
+def test_mixed_distance_equals_tree_distance_at_equal_counts(orc):
+    c = orc.Config(rows=2, cols=2, n=16, tournament=2, policy=orc.STEADY, bits=1, W=2,
+                   interval=1, seed=5)
+    G = 900
+    _, surf, _ = orc.run(c, generations=G)
+    tree = phylo.reconstruct(surf, c.policy, c.bits, c.W, G)
+    rng = np.random.default_rng(2)
+    for _ in range(100):
+        a, b = (int(v) for v in rng.choice(c.agents, size=2, replace=False))
+        m, _ = phylo.mrca_bounds_mixed(int(surf[a]), G, int(surf[b]), G, c.policy, c.bits, c.W)
+        assert 2 * G - 2 * m == phylo.pairwise_distance(tree, a, b)
