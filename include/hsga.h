@@ -317,6 +317,26 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
+/* Phylogeny reconstruction on the GPU from k sampled surfaces that all
+ * elapsed `generations` generations (synchronous mode, or free-running
+ * genomes of one counter), section "Distributed Phylogenetic Tracking": each
+ * genome's retained differentiae in ascending deposition time form a path in
+ * a trie; the trie with unifurcations collapsed (the root kept) is the tree.
+ * Nodes: 0 is the root (time -1); an internal node's time is the generation
+ * of the last differentia its genomes share; leaves (time = generations)
+ * follow the internal nodes, one per sample.  Outputs (host or device, all
+ * the same kind): parent_out / time_out (capacity >= 2k + 1 entries;
+ * parent of the root = -1), leaf_of_sample (k entries: the leaf node of
+ * sample i), *n_nodes (host).  surf: k uint64, host or device.  Node numbering
+ * other than the root's is unspecified.  deposit_interval as in hsga_config.
+ * Allocates scratch through the registered allocator; synchronous on
+ * cuda_stream.  HSGA_ERR_INVALID_ARG for k = 0, k > 2^28, policy NONE, a bad
+ * width or capacity. */
+int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t policy, uint32_t differentia_bits,
+                     uint32_t W, uint64_t generations, uint32_t deposit_interval,
+                     int64_t *parent_out, int64_t *time_out, uint32_t *leaf_of_sample,
+                     uint32_t capacity, uint32_t *n_nodes, void *cuda_stream);
+
 /* ------------------------------------------------------------ batches ---
  * Many independent runs (uneven grids, agents per island, policies,
  * mutation rates, seeds and generation budgets) advanced together: each

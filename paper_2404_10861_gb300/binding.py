@@ -92,6 +92,10 @@ _SIGS = {
     "hsga_get_async_log": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "hsga_get_migration_buffers": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
+    "hsga_reconstruct": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                          ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p], ctypes.c_int),
     "hsga_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_get_stats": ([ctypes.c_void_p, ctypes.POINTER(hsga_stats)], ctypes.c_int),
     "hsga_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
@@ -277,6 +281,26 @@ def hsga_get_migration_buffers(g, islands: int):
     _check(lib().hsga_get_migration_buffers(g, _ptr(chan), _ptr(inbuf)),
            "hsga_get_migration_buffers")
     return chan, inbuf
+
+
+def hsga_reconstruct(surf, policy, bits: int, W: int, generations: int, coarsen: int = 1,
+                     stream=None):
+    """GPU trie reconstruction of sampled surfaces (uint64 array of length k)
+    -> (parent, time, leaf_of_sample) numpy arrays; node 0 is the root."""
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    surf = np.ascontiguousarray(surf, dtype=np.uint64)
+    k = len(surf)
+    cap = 2 * k + 1
+    parent = np.zeros(cap, dtype=np.int64)
+    time = np.zeros(cap, dtype=np.int64)
+    leaf = np.zeros(k, dtype=np.uint32)
+    nodes = ctypes.c_uint32(0)
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().hsga_reconstruct(_ptr(surf), k, pol, bits, W, int(generations), int(coarsen),
+                                  _ptr(parent), _ptr(time), _ptr(leaf), cap,
+                                  ctypes.byref(nodes), s), "hsga_reconstruct")
+    n = nodes.value
+    return parent[:n], time[:n], leaf
 
 
 def hsga_synchronize(g):
