@@ -18,6 +18,7 @@ sharded, on this machine; timing is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -523,6 +524,67 @@ def run_async_wafer(args, mode="async"):
                       "data": "synthetic"}), flush=True)
 
 
+def run_reconstruct(args):
+    """Phylogeny reconstruction from sampled surfaces of the wafer-shaped grid
+    after 1,000 generations: the GPU trie (hsga_reconstruct, inputs and
+    outputs resident on the device) for 10,000 genomes (the paper's sample
+    size), 1M genomes and the whole 16.8M-agent population, beside the
+    oracle's reconstruction of the 10,000-genome sample on one host core."""
+    import time as _time
+    import torch
+    import oracle
+    from oracle import phylo
+    from paper_2404_10861_gb300 import _build, binding as hb
+    _build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    hb.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    G = 1000
+    with hb.Grid(stream=stream.cuda_stream, seed=1, **WORKLOAD) as g:
+        g.run(G)
+        _, surf = g.population()
+    rng = np.random.default_rng(0)
+    out = []
+    for k in (10_000, 1_000_000, AGENTS):
+        pick = rng.choice(AGENTS, size=k, replace=False) if k < AGENTS else np.arange(AGENTS)
+        s_dev = torch.from_numpy(surf[pick].view(np.int64)).cuda()
+        cap = 2 * k + 1
+        parent = torch.empty(cap, dtype=torch.int64, device="cuda")
+        tm = torch.empty(cap, dtype=torch.int64, device="cuda")
+        leaf = torch.empty(k, dtype=torch.int32, device="cuda")
+        nodes = ctypes.c_uint32(0)
+
+        def call():
+            hb._check(hb.lib().hsga_reconstruct(
+                s_dev.data_ptr(), k, 1, 1, 2, G, 1, parent.data_ptr(), tm.data_ptr(),
+                leaf.data_ptr(), cap, ctypes.byref(nodes), ctypes.c_void_p(stream.cuda_stream)),
+                "hsga_reconstruct")
+        for _ in range(args.warmup):
+            call()
+        reps = max(1, args.steps // 10)
+        t0 = _time.perf_counter()
+        for _ in range(reps):
+            call()
+        dt = (_time.perf_counter() - t0) / reps
+        out.append({"genomes": k, "ms": dt * 1e3, "genomes_per_s": k / dt,
+                    "nodes": nodes.value})
+    k = 10_000
+    pick = rng.choice(AGENTS, size=k, replace=False)
+    t0 = _time.perf_counter()
+    tree = phylo.reconstruct(surf[pick], 1, 1, 2, G)
+    cpu = _time.perf_counter() - t0
+    print(json.dumps({"metric": "genomes reconstructed/sec", "unit": "genomes/s",
+                      "workload": "trie reconstruction of sampled surfaces, wafer-shaped grid "
+                                  "(512x1024 islands x 32 agents) after 1,000 generations, "
+                                  "64-bit tilted surface, 1-bit differentiae",
+                      "gpu": out,
+                      "cpu_baseline": {"value": k / cpu, "unit": "genomes/s", "cores": 1,
+                                       "kind": "oracle", "sample": f"{k} genomes, "
+                                       f"{tree.n_nodes} nodes, {cpu:.2f} s"},
+                      "dtype": "u64", "data": "synthetic"}), flush=True)
+
+
 def run_profile(gens: int):
     """Workload only, for profilers: founders, `gens` generations, one sample."""
     import torch
@@ -548,7 +610,8 @@ def main():
                     help="profiling mode: only run this many generations of the workload "
                          "(no timing); used for ncu captures")
     ap.add_argument("--workload", default="wafer",
-                    choices=["wafer", "tiny", "mid", "batched", "served", "async", "buffered"],
+                    choices=["wafer", "tiny", "mid", "batched", "served", "async", "buffered",
+                             "reconstruct"],
                     help="wafer: the benchmark line; the others: informational lines")
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--memory-cap-mb", type=int, default=2048,
@@ -562,6 +625,9 @@ def main():
     args = ap.parse_args()
     if args.workload in ("async", "buffered"):
         run_async_wafer(args, args.workload)
+        return
+    if args.workload == "reconstruct":
+        run_reconstruct(args)
         return
     if args.workload == "batched":
         run_batched(args)
