@@ -27,7 +27,6 @@ _LIB = os.path.join(_HERE, "libhsga_oracle.so")
 STEADY, TILTED, STRETCHED, TRIVIAL, NONE, HYBRID = 0, 1, 2, 3, 4, 5
 POLICY_NAMES = {"steady": STEADY, "tilted": TILTED, "stretched": STRETCHED,
                 "trivial": TRIVIAL, "none": NONE, "hybrid": HYBRID}
-REC_WORDS = 6
 FITNESS_TRAIT, FITNESS_FLOAT = 0, 1
 
 
@@ -49,7 +48,8 @@ class _Cfg(ctypes.Structure):
                 ("W", ctypes.c_uint32), ("interval", ctypes.c_uint32),
                 ("p_ben", ctypes.c_double), ("p_del", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("coarsen", ctypes.c_uint32),
-                ("fitness", ctypes.c_uint32), ("sigma", ctypes.c_double)]
+                ("fitness", ctypes.c_uint32), ("sigma", ctypes.c_double),
+                ("words", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 @dataclass
@@ -63,7 +63,9 @@ class Config:
     the annotation interval (temporal coarsening: deposit every coarsen-th
     generation), and the fitness model: FITNESS_TRAIT (unsigned integer,
     mutations of one) or FITNESS_FLOAT (binary32, sign-restricted Gaussian
-    mutation amounts of standard deviation ``sigma``).
+    mutation amounts of standard deviation ``sigma``), and the surface width
+    in 64-bit words (``words``: S = 64 words / bits sites; surfaces are flat
+    agent-major arrays of agents x words uint64).
     """
     rows: int = 4
     cols: int = 4
@@ -79,6 +81,7 @@ class Config:
     coarsen: int = 1
     fitness: int = 0
     sigma: float = 1.0
+    words: int = 1
 
     @property
     def islands(self) -> int:
@@ -95,7 +98,7 @@ class Config:
     def _c(self) -> _Cfg:
         return _Cfg(self.rows, self.cols, self.n, self.tournament, self.policy,
                     self.bits, self.W, self.interval, self.p_ben, self.p_del,
-                    self.seed, self.coarsen, self.fitness, self.sigma)
+                    self.seed, self.coarsen, self.fitness, self.sigma, self.words, 0)
 
 
 _lib = None
@@ -186,7 +189,7 @@ def lookup(policy: int, S: int, W: int, T: int) -> np.ndarray:
 def founders(cfg: Config):
     """Founding population: every trait 0, every surface empty (all zero)."""
     return (np.zeros(cfg.agents, dtype=np.uint32),
-            np.zeros(cfg.agents, dtype=np.uint64))
+            np.zeros(cfg.agents * cfg.words, dtype=np.uint64))
 
 
 def run(cfg: Config, trait=None, surf=None, G0: int = 0, generations: int = 1,
@@ -227,7 +230,7 @@ def run_cone(cfg: Config, row: int, col: int, generations: int, G0: int = 0,
     """One island's agents after ``generations`` cycles from a uniform state,
     computed on its dependency cone only (exact at any torus size)."""
     t = np.zeros(cfg.n, dtype=np.uint32)
-    s = np.zeros(cfg.n, dtype=np.uint64)
+    s = np.zeros(cfg.n * cfg.words, dtype=np.uint64)
     c = cfg._c()
     rc = lib().orc_run_cone(ctypes.byref(c), row, col, trait0, surf0, G0,
                             generations, _p(t, ctypes.c_uint32),
@@ -238,10 +241,11 @@ def run_cone(cfg: Config, row: int, col: int, generations: int, G0: int = 0,
 
 
 def sample(cfg: Config, trait, surf, G: int, k: int):
-    """Step a7: k sampled genomes (k x 4 words) and their (island, slot)."""
+    """Step a7: k sampled genomes (k x (2 + 2 words) words: trait, surface
+    words as (low, high) pairs, G) and their (island, slot)."""
     trait = np.ascontiguousarray(trait, dtype=np.uint32)
     surf = np.ascontiguousarray(surf, dtype=np.uint64)
-    words = np.zeros((k, 4), dtype=np.uint32)
+    words = np.zeros((k, 2 + 2 * cfg.words), dtype=np.uint32)
     where = np.zeros((k, 2), dtype=np.uint32)
     c = cfg._c()
     rc = lib().orc_sample_grid(ctypes.byref(c), _p(trait, ctypes.c_uint32),
@@ -343,9 +347,10 @@ def sync_schedule(cfg: Config, G0: int, generations: int) -> np.ndarray:
 # ------------------------------------------- pieces for band decomposition ---
 
 def emigrate(cfg: Config, gid, trait, surf, G: int) -> np.ndarray:
-    """Step a1 for local islands with global ids ``gid``: (n_local, 6) records."""
+    """Step a1 for local islands with global ids ``gid``: (n_local, 4 + 2 words)
+    records (trait, direction, source index low/high, surface words)."""
     gid = np.ascontiguousarray(gid, dtype=np.uint32)
-    rec = np.zeros((len(gid), REC_WORDS), dtype=np.uint32)
+    rec = np.zeros((len(gid), 4 + 2 * cfg.words), dtype=np.uint32)
     c = cfg._c()
     lib().orc_emigrate(ctypes.byref(c), len(gid), _p(gid, ctypes.c_uint32),
                        _p(np.ascontiguousarray(trait, dtype=np.uint32), ctypes.c_uint32),

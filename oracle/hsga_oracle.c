@@ -211,7 +211,27 @@ typedef struct orc_cfg {
   uint32_t coarsen; /* annotate every coarsen-th generation (0 or 1: every one) */
   uint32_t fitness; /* ORC_FITNESS_TRAIT or ORC_FITNESS_FLOAT */
   double sigma;     /* ORC_FITNESS_FLOAT: standard deviation of the mutation amount */
+  uint32_t words;   /* surface width in 64-bit words (0 or 1: one) */
+  uint32_t pad;
 } orc_cfg;
+
+/* Surfaces of K = words 64-bit words per genome (agent-major: word w of
+ * agent a at surf[a K + w]) hold S = 64 K / bits sites; site s occupies bits
+ * [s b mod 64, s b mod 64 + b) of word floor(s b / 64) (b divides 64, so no
+ * field straddles two words).  K = 4 with 1-bit differentiae is the 256-bit
+ * field the paper draws ("Surface-based Hereditary Stratigraphy
+ * Algorithms"); wider differentiae and more sites are its suggested
+ * remedies for reconstruction precision ("Results › Clade Reconstruction
+ * Trial"). */
+static uint32_t orc_words(const orc_cfg *cfg) { return cfg->words > 1 ? cfg->words : 1; }
+
+static uint32_t orc_sites(const orc_cfg *cfg) { return 64u * orc_words(cfg) / cfg->bits; }
+
+static void orc_put_field(uint64_t *surface, uint32_t site, uint32_t bits, uint64_t value) {
+  uint64_t mask = (bits == 64) ? ~0ull : ((1ull << bits) - 1);
+  uint32_t word = site * bits / 64, shift = site * bits % 64;
+  surface[word] = (surface[word] & ~(mask << shift)) | ((value & mask) << shift);
+}
 
 /* Fitness models ("Methods › Genome Model" and "Results › On-hardware
  * Trial").  TRAIT: the first genome word is an unsigned integer fitness and
@@ -300,8 +320,9 @@ uint32_t orc_neighbour(const orc_cfg *cfg, uint32_t g, uint32_t d) {
 }
 
 /* An emigrant record: the copied genome, its direction and, for pedigree
- * tracking, the global agent index it was copied from. */
-#define ORC_REC_WORDS 6 /* trait, surf_lo, surf_hi, dir, src_lo, src_hi */
+ * tracking, the global agent index it was copied from: trait, dir, src_lo,
+ * src_hi, then the surface words as (low, high) 32-bit pairs. */
+static size_t orc_rec_words(const orc_cfg *cfg) { return 4 + 2 * (size_t)orc_words(cfg); }
 
 /* a1: emigrant records of the local islands (global ids gid[0..n_local)).
  * Population arrays are local: island l holds agents [l*n, l*n + n). */
@@ -314,13 +335,17 @@ void orc_emigrate(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
     uint32_t slot = orc_index(w[0], cfg->n);
     uint32_t dir = w[1] >> 30;
     uint64_t src = (uint64_t)gid[l] * cfg->n + slot;
-    uint32_t *r = rec + (size_t)l * ORC_REC_WORDS;
-    r[0] = trait[(size_t)l * cfg->n + slot];
-    r[1] = (uint32_t)surf[(size_t)l * cfg->n + slot];
-    r[2] = (uint32_t)(surf[(size_t)l * cfg->n + slot] >> 32);
-    r[3] = dir;
-    r[4] = (uint32_t)src;
-    r[5] = (uint32_t)(src >> 32);
+    uint32_t K = orc_words(cfg);
+    uint32_t *r = rec + (size_t)l * orc_rec_words(cfg);
+    size_t a = (size_t)l * cfg->n + slot;
+    r[0] = trait[a];
+    r[1] = dir;
+    r[2] = (uint32_t)src;
+    r[3] = (uint32_t)(src >> 32);
+    for (uint32_t w2 = 0; w2 < K; ++w2) {
+      r[4 + 2 * w2] = (uint32_t)surf[a * K + w2];
+      r[5 + 2 * w2] = (uint32_t)(surf[a * K + w2] >> 32);
+    }
   }
 }
 
@@ -338,14 +363,16 @@ void orc_immigrate(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
     orc_draw(cfg->seed, 0xFFFFFFFEu, gid[l], (uint32_t)G, 0, v);
     for (uint32_t d = 0; d < 4; ++d) {
       int32_t nb = nbr[(size_t)l * 4 + d];
-      const uint32_t *r = rec + (size_t)nb * ORC_REC_WORDS;
+      const uint32_t *r = rec + (size_t)nb * orc_rec_words(cfg);
       uint32_t toward_me = (d + 2) % 4; /* the neighbour must aim back at l */
-      if (r[3] != toward_me) continue;
+      if (r[1] != toward_me) continue;
       uint32_t slot = orc_index(v[d], cfg->n);
       size_t a = (size_t)l * cfg->n + slot;
+      uint32_t K = orc_words(cfg);
       trait[a] = r[0];
-      surf[a] = (uint64_t)r[1] | ((uint64_t)r[2] << 32);
-      if (src) src[a] = (uint64_t)r[4] | ((uint64_t)r[5] << 32);
+      for (uint32_t w2 = 0; w2 < K; ++w2)
+        surf[a * K + w2] = (uint64_t)r[4 + 2 * w2] | ((uint64_t)r[5 + 2 * w2] << 32);
+      if (src) src[a] = (uint64_t)r[2] | ((uint64_t)r[3] << 32);
     }
   }
 }
@@ -365,8 +392,8 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
                 const uint64_t *surf_in, const uint64_t *src, uint64_t G,
                 uint64_t T, uint32_t *trait_out, uint64_t *surf_out,
                 uint64_t *parent_out) {
-  uint32_t n = cfg->n;
-  uint32_t S = 64 / cfg->bits;
+  uint32_t n = cfg->n, K = orc_words(cfg);
+  uint32_t S = orc_sites(cfg);
   /* Temporal coarsening (the paper's suggestion to update annotations only
    * every k-th generation): generation T deposits only when k divides it,
    * as deposition number T / k. */
@@ -376,7 +403,6 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
   uint32_t site = annotate ? orc_site(cfg->policy, S, cfg->W, Td) : S;
   uint32_t site2 = (annotate && cfg->policy == ORC_HYBRID)
                        ? orc_hybrid_second_site(S, cfg->W, Td) : S;
-  uint64_t vmask = (cfg->bits == 64) ? ~0ull : ((1ull << cfg->bits) - 1);
   for (uint32_t l = 0; l < n_local; ++l) {
     if (active && !active[l]) continue;
     const uint32_t *fit = trait_in + (size_t)l * n; /* a3: fitness = trait */
@@ -398,24 +424,18 @@ void orc_select(const orc_cfg *cfg, uint32_t n_local, const uint32_t *gid,
         if (orc_fitter(cfg, fit[cand], fit[best])) best = cand;
       }
       size_t pa = (size_t)l * n + best;
-      uint64_t surface = surf_in[pa];
+      size_t ca = (size_t)l * n + j;
+      uint64_t *surface = surf_out + ca * K;
+      memcpy(surface, surf_in + pa * K, sizeof(uint64_t) * K);
       /* a5: mutation of the trait. */
       uint32_t trait = orc_mutate(cfg, trait_in[pa], w[2], j, gid[l], G);
       /* a6: deposit the new differentia (the hybrid policy's second one is
        * taken from bits 16.. of the same word). */
-      if (cfg->policy != ORC_NONE && site < S) {
-        uint32_t shift = site * cfg->bits;
-        surface &= ~(vmask << shift);
-        surface |= ((uint64_t)w[3] & vmask) << shift;
-      }
-      if (cfg->policy != ORC_NONE && site2 < S) {
-        uint32_t shift = site2 * cfg->bits;
-        surface &= ~(vmask << shift);
-        surface |= ((uint64_t)(w[3] >> 16) & vmask) << shift;
-      }
-      size_t ca = (size_t)l * n + j;
+      if (cfg->policy != ORC_NONE && site < S)
+        orc_put_field(surface, site, cfg->bits, w[3]);
+      if (cfg->policy != ORC_NONE && site2 < S)
+        orc_put_field(surface, site2, cfg->bits, w[3] >> 16);
       trait_out[ca] = trait;
-      surf_out[ca] = surface;
       if (parent_out)
         parent_out[ca] = src ? src[pa] : (uint64_t)gid[l] * n + best;
     }
@@ -447,12 +467,12 @@ int orc_run_grid(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
                  uint64_t G0, uint64_t n_gens, int premigrated,
                  uint64_t *parents) {
   uint32_t I = cfg->rows * cfg->cols;
-  size_t A = (size_t)I * cfg->n;
+  size_t A = (size_t)I * cfg->n, K = orc_words(cfg);
   uint32_t *gid = malloc(sizeof(uint32_t) * I);
   int32_t *nbr = malloc(sizeof(int32_t) * I * 4);
-  uint32_t *rec = malloc(sizeof(uint32_t) * ORC_REC_WORDS * I);
+  uint32_t *rec = malloc(sizeof(uint32_t) * orc_rec_words(cfg) * I);
   uint32_t *t2 = malloc(sizeof(uint32_t) * A);
-  uint64_t *s2 = malloc(sizeof(uint64_t) * A);
+  uint64_t *s2 = malloc(sizeof(uint64_t) * A * K);
   uint64_t *src = parents ? malloc(sizeof(uint64_t) * A) : NULL;
   if (!gid || !nbr || !rec || !t2 || !s2 || (parents && !src)) {
     free(gid); free(nbr); free(rec); free(t2); free(s2); free(src);
@@ -470,7 +490,7 @@ int orc_run_grid(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
     orc_select(cfg, I, gid, NULL, trait, surf, src, G, G, t2, s2,
                parents ? parents + (size_t)k * A : NULL);
     memcpy(trait, t2, sizeof(uint32_t) * A);
-    memcpy(surf, s2, sizeof(uint64_t) * A);
+    memcpy(surf, s2, sizeof(uint64_t) * A * K);
   }
   free(gid); free(nbr); free(rec); free(t2); free(s2); free(src);
   return 0;
@@ -482,7 +502,7 @@ int orc_migrate_grid(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
   uint32_t I = cfg->rows * cfg->cols;
   uint32_t *gid = malloc(sizeof(uint32_t) * I);
   int32_t *nbr = malloc(sizeof(int32_t) * I * 4);
-  uint32_t *rec = malloc(sizeof(uint32_t) * ORC_REC_WORDS * I);
+  uint32_t *rec = malloc(sizeof(uint32_t) * orc_rec_words(cfg) * I);
   if (!gid || !nbr || !rec) { free(gid); free(nbr); free(rec); return -1; }
   orc_torus_tables(cfg, gid, nbr);
   orc_emigrate(cfg, I, gid, trait, surf, G, rec);
@@ -503,13 +523,13 @@ int orc_run_cone(const orc_cfg *cfg, uint32_t r, uint32_t c, uint32_t trait0,
                  uint32_t *trait_out, uint64_t *surf_out) {
   uint32_t R = n_gens, D = 2 * R + 1, I = D * D, n = cfg->n;
   if (D > cfg->rows || D > cfg->cols) return -2;
-  size_t A = (size_t)I * n;
+  size_t A = (size_t)I * n, K = orc_words(cfg);
   uint32_t *gid = malloc(sizeof(uint32_t) * I);
   int32_t *nbr = malloc(sizeof(int32_t) * I * 4);
   uint8_t *active = malloc(I);
-  uint32_t *rec = malloc(sizeof(uint32_t) * ORC_REC_WORDS * I);
+  uint32_t *rec = malloc(sizeof(uint32_t) * orc_rec_words(cfg) * I);
   uint32_t *t1 = malloc(sizeof(uint32_t) * A), *t2 = malloc(sizeof(uint32_t) * A);
-  uint64_t *s1 = malloc(sizeof(uint64_t) * A), *s2 = malloc(sizeof(uint64_t) * A);
+  uint64_t *s1 = malloc(sizeof(uint64_t) * A * K), *s2 = malloc(sizeof(uint64_t) * A * K);
   if (!gid || !nbr || !active || !rec || !t1 || !t2 || !s1 || !s2) {
     free(gid); free(nbr); free(active); free(rec);
     free(t1); free(t2); free(s1); free(s2);
@@ -526,7 +546,10 @@ int orc_run_cone(const orc_cfg *cfg, uint32_t r, uint32_t c, uint32_t trait0,
       nbr[l * 4 + ORC_E] = x + 1 < D ? (int32_t)(l + 1) : -1;
       nbr[l * 4 + ORC_W] = x > 0 ? (int32_t)(l - 1) : -1;
     }
-  for (size_t a = 0; a < A; ++a) { t1[a] = trait0; s1[a] = surf0; }
+  for (size_t a = 0; a < A; ++a) {
+    t1[a] = trait0;
+    for (size_t w2 = 0; w2 < K; ++w2) s1[a * K + w2] = w2 == 0 ? surf0 : 0;
+  }
   for (uint32_t k = 0; k < n_gens; ++k) {
     uint64_t G = G0 + k;
     uint32_t radius = R - k - 1;
@@ -536,7 +559,7 @@ int orc_run_cone(const orc_cfg *cfg, uint32_t r, uint32_t c, uint32_t trait0,
         active[y * D + x] = (dy <= radius && dx <= radius);
       }
     memcpy(t2, t1, sizeof(uint32_t) * A);
-    memcpy(s2, s1, sizeof(uint64_t) * A);
+    memcpy(s2, s1, sizeof(uint64_t) * A * K);
     if (orc_migrates(cfg, G)) {
       /* Records of every island are computed; only those within the known
        * region are read by the active islands. */
@@ -549,16 +572,17 @@ int orc_run_cone(const orc_cfg *cfg, uint32_t r, uint32_t c, uint32_t trait0,
   }
   size_t centre = (size_t)(R * D + R) * n;
   memcpy(trait_out, t1 + centre, sizeof(uint32_t) * n);
-  memcpy(surf_out, s1 + centre, sizeof(uint64_t) * n);
+  memcpy(surf_out, s1 + centre * K, sizeof(uint64_t) * n * K);
   free(gid); free(nbr); free(active); free(rec);
   free(t1); free(t2); free(s1); free(s2);
   return 0;
 }
 
 /* a7: sample k genomes at generation G (one candidate per island, then k
- * distinct islands by partial Fisher-Yates).  out_words gets 4 words per
- * sample (trait, surf_lo, surf_hi, T=G); out_island_slot (may be NULL) gets
- * (island, slot).  Returns -2 if k exceeds the island count. */
+ * distinct islands by partial Fisher-Yates).  out_words gets 2 + 2K words
+ * per sample (trait, the surface words as (low, high) pairs, T=G: four words
+ * for a one-word surface); out_island_slot (may be NULL) gets (island,
+ * slot).  Returns -2 if k exceeds the island count. */
 int orc_sample_grid(const orc_cfg *cfg, const uint32_t *trait,
                     const uint64_t *surf, uint64_t G, uint32_t k,
                     uint32_t *out_words, uint32_t *out_island_slot) {
@@ -579,10 +603,14 @@ int orc_sample_grid(const orc_cfg *cfg, const uint32_t *trait,
     orc_draw(cfg->seed, 0xFFFFFFFDu, island, (uint32_t)G, 0, w);
     uint32_t slot = orc_index(w[0], cfg->n);
     size_t a = (size_t)island * cfg->n + slot;
-    out_words[4 * j + 0] = trait[a];
-    out_words[4 * j + 1] = (uint32_t)surf[a];
-    out_words[4 * j + 2] = (uint32_t)(surf[a] >> 32);
-    out_words[4 * j + 3] = (uint32_t)G;
+    uint32_t K = orc_words(cfg);
+    uint32_t *o = out_words + (size_t)j * (2 + 2 * K);
+    o[0] = trait[a];
+    for (uint32_t w2 = 0; w2 < K; ++w2) {
+      o[1 + 2 * w2] = (uint32_t)surf[a * K + w2];
+      o[2 + 2 * w2] = (uint32_t)(surf[a * K + w2] >> 32);
+    }
+    o[1 + 2 * K] = (uint32_t)G;
     if (out_island_slot) {
       out_island_slot[2 * j] = island;
       out_island_slot[2 * j + 1] = slot;
@@ -601,11 +629,10 @@ int orc_sample_grid(const orc_cfg *cfg, const uint32_t *trait,
  * place.  Returns 0 or -1 on allocation failure. */
 int orc_island_step(const orc_cfg *cfg, uint32_t i, uint64_t G, uint32_t *trait,
                     uint64_t *surf, uint32_t *tcount) {
-  uint32_t n = cfg->n;
-  uint32_t S = 64 / cfg->bits;
-  uint64_t vmask = (1ull << cfg->bits) - 1;
+  uint32_t n = cfg->n, K = orc_words(cfg);
+  uint32_t S = orc_sites(cfg);
   uint32_t *ct = malloc(sizeof(uint32_t) * n), *cT = malloc(sizeof(uint32_t) * n);
-  uint64_t *cs = malloc(sizeof(uint64_t) * n);
+  uint64_t *cs = malloc(sizeof(uint64_t) * n * K);
   if (!ct || !cT || !cs) {
     free(ct); free(cT); free(cs);
     return -1;
@@ -629,28 +656,22 @@ int orc_island_step(const orc_cfg *cfg, uint32_t i, uint64_t G, uint32_t *trait,
     }
     size_t pa = (size_t)i * n + best;
     uint32_t tr = orc_mutate(cfg, trait[pa], w[2], j, i, G);
-    uint64_t su = surf[pa];
+    uint64_t *su = cs + (size_t)j * K;
+    memcpy(su, surf + pa * K, sizeof(uint64_t) * K);
     uint32_t T = tcount[pa];
     if (cfg->policy != ORC_NONE) {
       uint32_t site = orc_site(cfg->policy, S, cfg->W, T);
-      if (site < S) {
-        su &= ~(vmask << (site * cfg->bits));
-        su |= ((uint64_t)w[3] & vmask) << (site * cfg->bits);
-      }
+      if (site < S) orc_put_field(su, site, cfg->bits, w[3]);
       if (cfg->policy == ORC_HYBRID) {
         uint32_t site2 = orc_hybrid_second_site(S, cfg->W, T);
-        if (site2 < S) {
-          su &= ~(vmask << (site2 * cfg->bits));
-          su |= ((uint64_t)(w[3] >> 16) & vmask) << (site2 * cfg->bits);
-        }
+        if (site2 < S) orc_put_field(su, site2, cfg->bits, w[3] >> 16);
       }
     }
     ct[j] = tr;
-    cs[j] = su;
     cT[j] = T + 1;
   }
   memcpy(trait + (size_t)i * n, ct, sizeof(uint32_t) * n);
-  memcpy(surf + (size_t)i * n, cs, sizeof(uint64_t) * n);
+  memcpy(surf + (size_t)i * n * K, cs, sizeof(uint64_t) * n * K);
   memcpy(tcount + (size_t)i * n, cT, sizeof(uint32_t) * n);
   free(ct); free(cT); free(cs);
   return 0;
@@ -680,6 +701,7 @@ int orc_island_step(const orc_cfg *cfg, uint32_t i, uint64_t G, uint32_t *trait,
 int orc_run_async(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
                   uint32_t *tcount, uint64_t G0, uint32_t n_gens,
                   const uint32_t *sched) {
+  if (orc_words(cfg) != 1) return -2;
   uint32_t I = cfg->rows * cfg->cols, n = cfg->n;
   /* emigrant records by island and generation: trait, lo, hi, T, dir */
   uint32_t *hist = malloc(sizeof(uint32_t) * 5 * (size_t)I * (n_gens + 1));
@@ -800,6 +822,7 @@ int orc_run_async(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
 int orc_run_buffered(const orc_cfg *cfg, uint32_t *trait, uint64_t *surf,
                      uint32_t *tcount, uint64_t G0, uint32_t n_gens,
                      const uint32_t *log, uint32_t *chan, uint32_t *inbuf) {
+  if (orc_words(cfg) != 1) return -2;
   uint32_t I = cfg->rows * cfg->cols, n = cfg->n;
   size_t C = (size_t)I * 4;
   uint32_t *mail = calloc(C * 4, sizeof(uint32_t));      /* genome in flight */

@@ -65,13 +65,17 @@ def true_mrca_generation(parents: np.ndarray, x: int, y: int) -> int:
 
 # ------------------------------------------------------------- surfaces ---
 
-def differentiae(surf: np.ndarray, bits: int) -> np.ndarray:
-    """(k, S) matrix of differentia values, site-major order."""
-    surf = np.asarray(surf, dtype=np.uint64).reshape(-1)
-    S = 64 // bits
-    shifts = (np.arange(S, dtype=np.uint64) * np.uint64(bits))
+def differentiae(surf: np.ndarray, bits: int, words: int = 1) -> np.ndarray:
+    """(k, S) matrix of differentia values in site order, S = 64 words / bits;
+    surf holds k genomes of `words` 64-bit words (agent-major), site s in bits
+    [s b mod 64, s b mod 64 + b) of word floor(s b / 64)."""
+    surf = np.asarray(surf, dtype=np.uint64).reshape(-1, words)
+    S = 64 * words // bits
+    site = np.arange(S)
+    word = site * bits // 64
+    shifts = (site * bits % 64).astype(np.uint64)
     mask = np.uint64((1 << bits) - 1)
-    return ((surf[:, None] >> shifts[None, :]) & mask).astype(np.int64)
+    return ((surf[:, word] >> shifts[None, :]) & mask).astype(np.int64)
 
 
 def retained_order(policy: int, S: int, W: int, T: int, coarsen: int = 1):
@@ -178,12 +182,12 @@ class Tree:
 
 
 def reconstruct(surf: np.ndarray, policy: int, bits: int, W: int, T: int,
-                coarsen: int = 1) -> Tree:
-    """Trie reconstruction from sampled surfaces that all elapsed T
-    generations."""
-    S = 64 // bits
+                coarsen: int = 1, words: int = 1) -> Tree:
+    """Trie reconstruction from sampled surfaces (of `words` 64-bit words
+    each) that all elapsed T generations."""
+    S = 64 * words // bits
     order, times = retained_order(policy, S, W, T, coarsen)
-    D = differentiae(surf, bits)[:, order]
+    D = differentiae(surf, bits, words)[:, order]
     parent, time = [-1], [-1]
     kids = [dict()]  # per node: value -> child node
     leaf_of_sample = []

@@ -73,3 +73,41 @@ def test_coarsened_ancestry_bounds(orc):
         x, y = rng.choice(c.agents, size=2, replace=False)
         d_true = phylo.true_mrca_generation(par, int(x), int(y))
         assert np.array_equal(D[x, times < d_true], D[y, times < d_true])
+
+
+@pytest.mark.parametrize("policy,bits,words,W", [(1, 1, 4, 2), (0, 2, 2, 2), (2, 16, 4, 1),
+                                                 (5, 4, 2, 2), (3, 8, 4, 2)])
+def test_wide_surfaces_hold_their_ancestors_draws(orc, policy, bits, words, W):
+    """Surfaces of several 64-bit words (up to the 256-bit field): every
+    retained differentia is the value its own ancestor drew when it was
+    deposited (word 3 of the Philox block of the child on the lineage, bits
+    16.. for the hybrid policy's tilted half), found by walking the pedigree
+    and recomputing the draw; selection never depends on the surface, so
+    traits equal those of the one-word run."""
+    from oracle import phylo
+    c = orc.Config(rows=3, cols=3, n=8, tournament=2, policy=policy, bits=bits, W=W,
+                   interval=1, p_ben=0.05, seed=21, words=words)
+    G = 300
+    trait, surf, par = orc.run(c, generations=G, track_parents=True)
+    narrow = orc.Config(**{**c.__dict__, "words": 1, "bits": 1, "W": 2, "policy": 0})
+    t1, _, _ = orc.run(narrow, generations=G)
+    assert np.array_equal(trait, t1)
+    S = 64 * words // bits
+    times = orc.lookup(policy, S, W, G)
+    D = phylo.differentiae(surf, bits, words)
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    half = S // 2
+    rng = np.random.default_rng(0)
+    checked = 0
+    for x in rng.choice(c.agents, size=12, replace=False):
+        line = phylo.lineage(par, int(x))
+        for site, t in enumerate(times):
+            if t < 0:
+                continue
+            child = int(line[t + 1])                     # the lineage's child born at t
+            w3 = int(orc.philox4x32(key, (child % c.n, child // c.n, int(t), 1))[3])
+            second = policy == 5 and site >= half
+            want = ((w3 >> 16) if second else w3) & ((1 << bits) - 1)
+            assert D[x, site] == want, (x, site, t)
+            checked += 1
+    assert checked >= 12 * 8
