@@ -557,7 +557,7 @@ def run_reconstruct(args):
 
         def call():
             hb._check(hb.lib().hsga_reconstruct(
-                s_dev.data_ptr(), k, 1, 1, 2, G, 1, parent.data_ptr(), tm.data_ptr(),
+                s_dev.data_ptr(), k, 1, 1, 1, 2, G, 1, parent.data_ptr(), tm.data_ptr(),
                 leaf.data_ptr(), cap, ctypes.byref(nodes), ctypes.c_void_p(stream.cuda_stream)),
                 "hsga_reconstruct")
         for _ in range(args.warmup):

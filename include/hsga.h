@@ -142,13 +142,25 @@ typedef enum hsga_fitness {
   HSGA_FITNESS_FLOAT = 1
 } hsga_fitness;
 
+/* Surface width (sections "Surface-based Hereditary Stratigraphy
+ * Algorithms", whose figure shows a 256-bit field, and "Results › Clade
+ * Reconstruction Trial", which names more and wider differentiae as the
+ * remedy for reconstruction precision).  A surface is K = surface_words
+ * 64-bit words holding S = 64 K / differentia_bits sites; site s occupies
+ * bits [s b mod 64, s b mod 64 + b) of word floor(s b / 64).  Population
+ * arrays hold K words per agent, agent-major (word w of agent a at
+ * surf[a K + w]); sample records are 2 + 2K words (trait, the surface words
+ * as (low, high) 32-bit pairs, T), i.e. four words when K = 1.  K > 1 needs
+ * synchronous migration, a surface policy, agents_per_island <= 32 and the
+ * AUTO or STREAMED kernel (a warp-per-island path); fossil sampling,
+ * batches and the allocation-free entry point need K = 1. */
 /* Run configuration (plain data, caller-owned; copied by hsga_init_grid). */
 typedef struct hsga_config {
   uint32_t rows, cols;          /* toroidal island grid, each >= 1 */
   uint32_t agents_per_island;   /* n, 1..64 (the paper's runs use 32) */
   uint32_t tournament_size;     /* 1..64 (the paper uses 5) */
   uint32_t surface_policy;      /* hsga_policy */
-  uint32_t differentia_bits;    /* b in {1,2,4,8}; S = 64 / b sites */
+  uint32_t differentia_bits;    /* b in {1,2,4,8,16}; S = 64 K / b sites */
   uint32_t sites_per_level;     /* W for tilted / stretched: 1, 2 or 4, S/W >= 2 */
   uint32_t migration_interval;  /* migrate when G % interval == 0; 0 = never */
   double p_beneficial;          /* in [0,1]; p_beneficial + p_deleterious <= 1 */
@@ -161,7 +173,8 @@ typedef struct hsga_config {
   uint32_t migration_mode;      /* hsga_migration_mode */
   uint32_t fitness;             /* hsga_fitness */
   double mutation_sigma;        /* FLOAT: standard deviation of mutation amounts, > 0 */
-  uint64_t reserved;            /* must be 0 */
+  uint32_t surface_words;       /* K: surface width in 64-bit words, 1 (0), 2 or 4 */
+  uint32_t reserved;            /* must be 0 */
 } hsga_config;
 
 typedef struct hsga_stats {
@@ -295,7 +308,7 @@ int hsga_load(hsga_grid *g, const void *buf, size_t len);
 void hsga_destroy(hsga_grid *g);
 
 /* Site written by deposition number T (T < 2^32 - 1) under `policy` with S
- * sites (power of two, 8..64) and W sites per level; returns S when the
+ * sites (power of two, 2..256) and W sites per level; returns S when the
  * policy discards that deposition.  Host function. */
 uint32_t hsga_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T);
 
@@ -317,7 +330,8 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
-/* Phylogeny reconstruction on the GPU from k sampled surfaces that all
+/* Phylogeny reconstruction on the GPU from k sampled surfaces (of
+ * surface_words 64-bit words each, agent-major; 0 means 1) that all
  * elapsed `generations` generations (synchronous mode, or free-running
  * genomes of one counter), section "Distributed Phylogenetic Tracking": each
  * genome's retained differentiae in ascending deposition time form a path in
@@ -327,13 +341,15 @@ int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
  * follow the internal nodes, one per sample.  Outputs (host or device, all
  * the same kind): parent_out / time_out (capacity >= 2k + 1 entries;
  * parent of the root = -1), leaf_of_sample (k entries: the leaf node of
- * sample i), *n_nodes (host).  surf: k uint64, host or device.  Node numbering
+ * sample i), *n_nodes (host).  surf: k * surface_words uint64, host or
+ * device.  Node numbering
  * other than the root's is unspecified.  deposit_interval as in hsga_config.
  * Allocates scratch through the registered allocator; synchronous on
  * cuda_stream.  HSGA_ERR_INVALID_ARG for k = 0, k > 2^28, policy NONE, a bad
  * width or capacity. */
-int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t policy, uint32_t differentia_bits,
-                     uint32_t W, uint64_t generations, uint32_t deposit_interval,
+int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t surface_words, uint32_t policy,
+                     uint32_t differentia_bits, uint32_t W, uint64_t generations,
+                     uint32_t deposit_interval,
                      int64_t *parent_out, int64_t *time_out, uint32_t *leaf_of_sample,
                      uint32_t capacity, uint32_t *n_nodes, void *cuda_stream);
 

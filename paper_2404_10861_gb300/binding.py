@@ -42,7 +42,7 @@ class hsga_config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("kernel", ctypes.c_uint32),
                 ("deposit_interval", ctypes.c_uint32), ("migration_mode", ctypes.c_uint32),
                 ("fitness", ctypes.c_uint32), ("mutation_sigma", ctypes.c_double),
-                ("reserved", ctypes.c_uint64)]
+                ("surface_words", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class hsga_stats(ctypes.Structure):
@@ -93,7 +93,8 @@ _SIGS = {
     "hsga_get_migration_buffers": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
     "hsga_reconstruct": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
-                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                          ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                          ctypes.c_void_p,
                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                           ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p], ctypes.c_int),
     "hsga_synchronize": ([ctypes.c_void_p], ctypes.c_int),
@@ -203,14 +204,15 @@ def use_default_allocator():
 # ------------------------------------------------------------ functions ---
 def make_config(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, W=2,
                 interval=1, p_ben=0.0, p_del=0.0, seed=1, kernel=KERNEL_AUTO,
-                coarsen=1, mode="sync", fitness="trait", sigma=0.0) -> hsga_config:
+                coarsen=1, mode="sync", fitness="trait", sigma=0.0, words=1) -> hsga_config:
     """fitness "trait": unsigned integer fitness, mutations of one; "float":
     binary32 fitness with sign-restricted Gaussian mutation amounts of
-    standard deviation ``sigma`` (> 0)."""
+    standard deviation ``sigma`` (> 0).  words: surface width in 64-bit words
+    (1, 2 or 4; S = 64 words / bits sites)."""
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return hsga_config(rows, cols, n, tournament, pol, bits, W, interval, p_ben, p_del,
                        seed, kernel, coarsen, {"sync": 0, "async": 1, "buffered": 2}[mode],
-                       {"trait": 0, "float": 1}[fitness], sigma, 0)
+                       {"trait": 0, "float": 1}[fitness], sigma, words, 0)
 
 
 def hsga_init_grid(cfg: hsga_config, cuda_stream=None) -> ctypes.c_void_p:
@@ -284,19 +286,21 @@ def hsga_get_migration_buffers(g, islands: int):
 
 
 def hsga_reconstruct(surf, policy, bits: int, W: int, generations: int, coarsen: int = 1,
-                     stream=None):
-    """GPU trie reconstruction of sampled surfaces (uint64 array of length k)
-    -> (parent, time, leaf_of_sample) numpy arrays; node 0 is the root."""
+                     stream=None, words: int = 1):
+    """GPU trie reconstruction of sampled surfaces (k x words uint64,
+    agent-major) -> (parent, time, leaf_of_sample) numpy arrays; node 0 is
+    the root."""
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
-    surf = np.ascontiguousarray(surf, dtype=np.uint64)
-    k = len(surf)
+    surf = np.ascontiguousarray(surf, dtype=np.uint64).reshape(-1)
+    k = len(surf) // max(1, words)
     cap = 2 * k + 1
     parent = np.zeros(cap, dtype=np.int64)
     time = np.zeros(cap, dtype=np.int64)
     leaf = np.zeros(k, dtype=np.uint32)
     nodes = ctypes.c_uint32(0)
     s = None if stream is None else ctypes.c_void_p(int(stream))
-    _check(lib().hsga_reconstruct(_ptr(surf), k, pol, bits, W, int(generations), int(coarsen),
+    _check(lib().hsga_reconstruct(_ptr(surf), k, words, pol, bits, W, int(generations),
+                                  int(coarsen),
                                   _ptr(parent), _ptr(time), _ptr(leaf), cap,
                                   ctypes.byref(nodes), s), "hsga_reconstruct")
     n = nodes.value
@@ -492,9 +496,13 @@ class Grid:
     def set_population(self, trait, surf, generation):
         hsga_set_population(self.handle, trait, surf, generation)
 
+    @property
+    def words(self) -> int:
+        return max(1, self.cfg.surface_words)
+
     def population(self):
         t = np.zeros(self.agents, dtype=np.uint32)
-        s = np.zeros(self.agents, dtype=np.uint64)
+        s = np.zeros(self.agents * self.words, dtype=np.uint64)
         hsga_get_population(self.handle, t, s)
         return t, s
 
@@ -513,7 +521,7 @@ class Grid:
         hsga_migrate(self.handle)
 
     def sample(self, k):
-        w = np.zeros((k, 4), dtype=np.uint32)
+        w = np.zeros((k, 2 + 2 * self.words), dtype=np.uint32)
         where = np.zeros((k, 2), dtype=np.uint32)
         hsga_sample_surfaces(self.handle, k, w, where)
         return w, where

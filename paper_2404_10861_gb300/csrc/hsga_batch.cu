@@ -414,7 +414,8 @@ int hsga_batch_add(hsga_batch *b, const hsga_config *cfg, uint64_t generations,
   if (!b || !run_id) return HSGA_ERR_INVALID_ARG;
   const int v = validate_config(cfg);
   if (v != HSGA_OK) return v;
-  if (cfg->migration_mode != HSGA_MIGRATION_SYNC || cfg->fitness != HSGA_FITNESS_TRAIT)
+  if (cfg->migration_mode != HSGA_MIGRATION_SYNC || cfg->fitness != HSGA_FITNESS_TRAIT ||
+      cfg->surface_words > 1)
     return HSGA_ERR_UNSUPPORTED;
   if (b->tick + generations > kMaxTick) return HSGA_ERR_INVALID_ARG;
   HostRun R;

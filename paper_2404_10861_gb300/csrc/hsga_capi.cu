@@ -34,6 +34,9 @@ struct hsga_grid {
   Allocator alloc;
   cudaStream_t stream = nullptr;
   uint64_t agents = 0;
+  uint64_t swords = 0;     // surface words in a population: agents x K
+  bool wide = false;       // K > 1
+  uint64_t *wrec = nullptr;  // wide migrant records: islands x (K + 1)
   uint32_t *trait[2] = {nullptr, nullptr};
   uint64_t *surf[2] = {nullptr, nullptr};
   int cur = 0;
@@ -116,8 +119,10 @@ int validate(const hsga_config *c) {
   if (c->tournament_size == 0 || c->tournament_size > 64) return HSGA_ERR_INVALID_ARG;
   if (c->surface_policy > HSGA_HYBRID) return HSGA_ERR_INVALID_ARG;
   const uint32_t b = c->differentia_bits;
-  if (!(b == 1 || b == 2 || b == 4 || b == 8)) return HSGA_ERR_INVALID_ARG;
-  const uint32_t S = 64 / b, W = c->sites_per_level;
+  if (!(b == 1 || b == 2 || b == 4 || b == 8 || b == 16)) return HSGA_ERR_INVALID_ARG;
+  const uint32_t K = c->surface_words;
+  if (!(K <= 2 || K == 4)) return HSGA_ERR_INVALID_ARG;
+  const uint32_t S = 64 * (K > 1 ? K : 1) / b, W = c->sites_per_level;
   if (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED) {
     if (!(W == 1 || W == 2 || W == 4) || S / W < 2) return HSGA_ERR_INVALID_ARG;
   }
@@ -129,6 +134,12 @@ int validate(const hsga_config *c) {
   if (c->p_beneficial + c->p_deleterious > 1.0) return HSGA_ERR_INVALID_ARG;
   if (c->kernel > HSGA_KERNEL_RESIDENT_GRID || c->reserved != 0) return HSGA_ERR_INVALID_ARG;
   if (c->fitness > HSGA_FITNESS_FLOAT) return HSGA_ERR_INVALID_ARG;
+  if (K > 1) {  // wide surfaces: the synchronous warp-per-island path
+    if (c->surface_policy == HSGA_NONE || c->agents_per_island > 32) return HSGA_ERR_INVALID_ARG;
+    if (c->migration_mode != HSGA_MIGRATION_SYNC) return HSGA_ERR_UNSUPPORTED;
+    if (c->kernel != HSGA_KERNEL_AUTO && c->kernel != HSGA_KERNEL_STREAMED)
+      return HSGA_ERR_UNSUPPORTED;
+  }
   if (c->fitness == HSGA_FITNESS_FLOAT) {
     if (!(c->mutation_sigma > 0.0 && c->mutation_sigma < 1e30)) return HSGA_ERR_INVALID_ARG;
     if (c->agents_per_island > 32) return HSGA_ERR_INVALID_ARG;
@@ -156,7 +167,8 @@ RunParams make_params(const hsga_config *c) {
   p.k1 = (uint32_t)(c->seed >> 32);
   p.policy = c->surface_policy;
   p.bits = c->differentia_bits;
-  p.S = 64 / p.bits;
+  p.words = c->surface_words > 1 ? c->surface_words : 1;
+  p.S = 64 * p.words / p.bits;
   p.W = (c->surface_policy == HSGA_TILTED || c->surface_policy == HSGA_STRETCHED ||
          c->surface_policy == HSGA_HYBRID)
             ? c->sites_per_level
@@ -201,6 +213,7 @@ void free_grid(hsga_grid *g) {
     dev_free(g->alloc, g->surf[i], g->stream);
   }
   dev_free(g->alloc, g->rec, g->stream);
+  dev_free(g->alloc, g->wrec, g->stream);
   dev_free(g->alloc, g->flags, g->stream);
   dev_free(g->alloc, g->err, g->stream);
   dev_free(g->alloc, g->sample_scratch, g->stream);
@@ -298,10 +311,12 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
   g->alloc = g_allocator;
   g->stream = (cudaStream_t)cuda_stream;
   g->agents = (uint64_t)g->p.islands * g->p.n;
+  g->swords = g->agents * g->p.words;
+  g->wide = g->p.words > 1;
   const bool tracked = cfg->surface_policy != HSGA_NONE;
   for (int i = 0; i < 2; ++i) {
     g->trait[i] = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->agents, g->stream);
-    g->surf[i] = tracked ? (uint64_t *)dev_alloc(g->alloc, sizeof(uint64_t) * g->agents, g->stream)
+    g->surf[i] = tracked ? (uint64_t *)dev_alloc(g->alloc, sizeof(uint64_t) * g->swords, g->stream)
                          : nullptr;
   }
   g->rec = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
@@ -328,6 +343,14 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
       return HSGA_ERR_CUDA;
     }
   }
+  if (g->wide) {
+    g->wrec = (uint64_t *)dev_alloc(g->alloc, sizeof(uint64_t) * (g->p.words + 1) *
+                                                  (size_t)g->p.islands, g->stream);
+    if (!g->wrec) {
+      free_grid(g);
+      return HSGA_ERR_OOM;
+    }
+  }
   g->flags = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->p.islands, g->stream);
   g->err = (int *)dev_alloc(g->alloc, sizeof(int), g->stream);
   bool ok = g->trait[0] && g->trait[1] && g->rec && g->flags && g->err &&
@@ -338,7 +361,7 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
   }
   cudaError_t e = cudaMemsetAsync(g->trait[0], 0, sizeof(uint32_t) * g->agents, g->stream);
   if (e == cudaSuccess && tracked)
-    e = cudaMemsetAsync(g->surf[0], 0, sizeof(uint64_t) * g->agents, g->stream);
+    e = cudaMemsetAsync(g->surf[0], 0, sizeof(uint64_t) * g->swords, g->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e != cudaSuccess || reset_sync_state(g) != HSGA_OK) {
@@ -346,7 +369,7 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
     return HSGA_ERR_CUDA;
   }
   g->resident = false;
-  if (cfg->kernel != HSGA_KERNEL_STREAMED && !g->async && !g->p.flt) {
+  if (cfg->kernel != HSGA_KERNEL_STREAMED && !g->async && !g->p.flt && !g->wide) {
     g->resident = resident_plan(g->p, &g->plan, cfg->kernel == HSGA_KERNEL_RESIDENT_GRID);
     if (!g->resident && cfg->kernel >= HSGA_KERNEL_RESIDENT) {
       free_grid(g);
@@ -365,7 +388,7 @@ int hsga_set_population(hsga_grid *g, const uint32_t *trait, const uint64_t *sur
   g->cur = 0;
   cudaError_t e = copy_in(g->trait[0], trait, sizeof(uint32_t) * g->agents, g->stream);
   if (e == cudaSuccess && tracked)
-    e = copy_in(g->surf[0], surf, sizeof(uint64_t) * g->agents, g->stream);
+    e = copy_in(g->surf[0], surf, sizeof(uint64_t) * g->swords, g->stream);
   if (e != cudaSuccess) return HSGA_ERR_CUDA;
   g->G = generation;
   if (g->async && fill_u32(g->tcount, (uint32_t)generation, g->agents, g->stream) != cudaSuccess)
@@ -385,11 +408,11 @@ int hsga_get_population(hsga_grid *g, uint32_t *trait, uint64_t *surf) {
                                   cudaMemcpyDefault, g->stream);
   if (e == cudaSuccess && surf) {
     if (tracked)
-      e = cudaMemcpyAsync(surf, g->surf[g->cur], sizeof(uint64_t) * g->agents, cudaMemcpyDefault,
+      e = cudaMemcpyAsync(surf, g->surf[g->cur], sizeof(uint64_t) * g->swords, cudaMemcpyDefault,
                           g->stream);
     else
-      e = is_device_ptr(surf) ? cudaMemsetAsync(surf, 0, sizeof(uint64_t) * g->agents, g->stream)
-                              : (memset(surf, 0, sizeof(uint64_t) * g->agents), cudaSuccess);
+      e = is_device_ptr(surf) ? cudaMemsetAsync(surf, 0, sizeof(uint64_t) * g->swords, g->stream)
+                              : (memset(surf, 0, sizeof(uint64_t) * g->swords), cudaSuccess);
   }
   if (e != cudaSuccess) return HSGA_ERR_CUDA;
   if (!is_device_ptr(trait) || (surf && !is_device_ptr(surf)))
@@ -488,6 +511,21 @@ int advance(hsga_grid *g, uint64_t n) {
       g->launches++;
       done += m;
     }
+  } else if (g->wide) {
+    // surfaces of several words: explicit a1 + a2, then one warp per island
+    for (uint64_t k = 0; k < n && e == cudaSuccess; ++k) {
+      const uint64_t G = g->G + k;
+      if (migrates(g->p, G) && !(g->premigrated && k == 0)) {
+        e = launch_migrate_wide(g->p, (uint32_t)G, g->trait[g->cur], g->surf[g->cur], g->wrec,
+                                g->stream);
+        g->launches += 2;
+      }
+      if (e == cudaSuccess)
+        e = launch_step_wide(g->p, (uint32_t)G, g->trait[g->cur], g->surf[g->cur],
+                             g->trait[1 - g->cur], g->surf[1 - g->cur], g->stream);
+      g->cur = 1 - g->cur;
+      g->launches++;
+    }
   } else if (g->p.flt) {
     // float fitness, synchronous: explicit a1 + a2, then one warp per island
     for (uint64_t k = 0; k < n && e == cudaSuccess; ++k) {
@@ -523,6 +561,7 @@ int advance(hsga_grid *g, uint64_t n) {
 
 int hsga_set_fossil_sampling(hsga_grid *g, uint64_t every, uint32_t k, uint32_t capacity) {
   if (!g) return HSGA_ERR_INVALID_ARG;
+  if (g->wide && every) return HSGA_ERR_UNSUPPORTED;
   if (every && (k == 0 || k > g->p.islands || capacity < k)) return HSGA_ERR_INVALID_ARG;
   dev_free(g->alloc, g->fossil_words, g->stream);
   dev_free(g->alloc, g->fossil_where, g->stream);
@@ -631,8 +670,10 @@ int hsga_migrate(hsga_grid *g) {
   if (g->broken) return HSGA_ERR_DEVICE;
   if (g->async) return HSGA_ERR_UNSUPPORTED;
   if (g->premigrated) return HSGA_ERR_INVALID_ARG;
-  cudaError_t e = launch_migrate(g->p, (uint32_t)g->G, g->trait[g->cur], g->surf[g->cur], g->rec,
-                                 g->stream);
+  cudaError_t e = g->wide ? launch_migrate_wide(g->p, (uint32_t)g->G, g->trait[g->cur],
+                                                g->surf[g->cur], g->wrec, g->stream)
+                          : launch_migrate(g->p, (uint32_t)g->G, g->trait[g->cur],
+                                           g->surf[g->cur], g->rec, g->stream);
   g->launches += 2;
   if (e != cudaSuccess) return HSGA_ERR_CUDA;
   g->premigrated = true;
@@ -646,6 +687,29 @@ int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
   if (k == 0) return HSGA_OK;
   const int sr = ensure_sample_scratch(g, k);
   if (sr != HSGA_OK) return sr;
+  if (g->wide) {
+    // pick (island, slot) as for one-word surfaces, then gather wide records
+    const size_t rw = 2 + 2 * (size_t)g->p.words;
+    uint32_t *staging = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * (6 + rw) * (size_t)k,
+                                              g->stream);
+    if (!staging) return HSGA_ERR_OOM;
+    uint32_t *pick = staging + 4 * (size_t)k, *wide = staging + 6 * (size_t)k;
+    cudaError_t e = launch_sample(g->p, (uint32_t)g->G, k, g->trait[g->cur], nullptr, staging,
+                                  pick, g->sample_scratch, g->stream, nullptr);
+    if (e == cudaSuccess)
+      e = launch_gather_wide(g->p, (uint32_t)g->G, k, g->trait[g->cur], g->surf[g->cur], pick,
+                             wide, g->stream);
+    g->launches += 2;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out_words, wide, sizeof(uint32_t) * rw * k, cudaMemcpyDefault,
+                          g->stream);
+    if (e == cudaSuccess && out_island_slot)
+      e = cudaMemcpyAsync(out_island_slot, pick, sizeof(uint32_t) * 2 * k, cudaMemcpyDefault,
+                          g->stream);
+    dev_free(g->alloc, staging, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    return cuda_status(e);
+  }
   // the kernels store 16-byte records and 8-byte pairs: misaligned device
   // outputs go through the staging buffer like host outputs
   const bool dev_words = is_device_ptr(out_words) && ((uintptr_t)out_words % 16) == 0;
@@ -706,7 +770,7 @@ int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
 int hsga_save(hsga_grid *g, void *buf, size_t *len) {
   if (!g || !len) return HSGA_ERR_INVALID_ARG;
   if (g->async) return HSGA_ERR_UNSUPPORTED;
-  const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 12;
+  const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 4 + g->swords * 8;
   if (!buf) {
     *len = need;
     return HSGA_OK;
@@ -719,10 +783,10 @@ int hsga_save(hsga_grid *g, void *buf, size_t *len) {
   uint32_t *t = (uint32_t *)(p + 16 + sizeof(hsga_config));
   uint64_t *s = (uint64_t *)(t + g->agents);
   // surfaces may be unaligned for uint64 in the caller's buffer: stage via get_population
-  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (g->agents ? g->agents : 1));
+  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (g->swords ? g->swords : 1));
   if (!tmp) return HSGA_ERR_OOM;
   int r = hsga_get_population(g, t, tmp);
-  if (r == HSGA_OK) memcpy(s, tmp, sizeof(uint64_t) * g->agents);
+  if (r == HSGA_OK) memcpy(s, tmp, sizeof(uint64_t) * g->swords);
   free(tmp);
   if (r == HSGA_OK) *len = need;
   return r;
@@ -731,7 +795,7 @@ int hsga_save(hsga_grid *g, void *buf, size_t *len) {
 int hsga_load(hsga_grid *g, const void *buf, size_t len) {
   if (!g || !buf) return HSGA_ERR_INVALID_ARG;
   if (g->async) return HSGA_ERR_UNSUPPORTED;
-  const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 12;
+  const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 4 + g->swords * 8;
   if (len < need) return HSGA_ERR_INVALID_ARG;
   const char *p = (const char *)buf;
   uint64_t magic = 0, G = 0;
@@ -740,7 +804,7 @@ int hsga_load(hsga_grid *g, const void *buf, size_t len) {
   if (memcmp(p + 8, &g->cfg, sizeof(hsga_config)) != 0) return HSGA_ERR_INVALID_ARG;
   memcpy(&G, p + 8 + sizeof(hsga_config), 8);
   const uint32_t *t = (const uint32_t *)(p + 16 + sizeof(hsga_config));
-  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (g->agents ? g->agents : 1));
+  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (g->swords ? g->swords : 1));
   uint32_t *tt = (uint32_t *)malloc(sizeof(uint32_t) * (g->agents ? g->agents : 1));
   if (!tmp || !tt) {
     free(tmp);
@@ -748,7 +812,7 @@ int hsga_load(hsga_grid *g, const void *buf, size_t len) {
     return HSGA_ERR_OOM;
   }
   memcpy(tt, t, sizeof(uint32_t) * g->agents);
-  memcpy(tmp, t + g->agents, sizeof(uint64_t) * g->agents);
+  memcpy(tmp, t + g->agents, sizeof(uint64_t) * g->swords);
   int r = hsga_set_population(g, tt, tmp, G);
   free(tmp);
   free(tt);
@@ -767,7 +831,7 @@ uint32_t hsga_site(uint32_t policy, uint32_t S, uint32_t W, uint64_t T) {
 
 // Closed-form timestamp lookup (see hsga.h for the site functions it inverts).
 int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *out) {
-  if (!out || !power_of_two(S) || S < 2 || S > 64 || policy > HSGA_HYBRID)
+  if (!out || !power_of_two(S) || S < 2 || S > 256 || policy > HSGA_HYBRID)
     return HSGA_ERR_INVALID_ARG;
   if (policy == HSGA_HYBRID) {  // steady half, then tilted half
     if (S < 4) return HSGA_ERR_INVALID_ARG;
@@ -818,7 +882,15 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *ou
   const uint32_t L = S / W;
   for (uint32_t lvl = 0; lvl < L; ++lvl) {
     const bool capped = lvl == L - 1;
-    const uint64_t c = capped ? (N >> (L - 1)) : ((N + (1ull << lvl)) >> (lvl + 1));
+    // depositions so far with ctz(t + 1) == lvl (or >= lvl for the capped
+    // level); none at lvl >= 64 for a 64-bit count
+    uint64_t c;
+    if (capped)
+      c = lvl >= 64 ? 0 : (N >> lvl);
+    else if (lvl >= 63)
+      c = lvl == 63 && N >= (1ull << 63) ? 1 : 0;
+    else
+      c = (N + (1ull << lvl)) >> (lvl + 1);
     for (uint32_t r = 0; r < W; ++r) {
       uint64_t idx;
       if (policy == HSGA_TILTED) {
@@ -838,7 +910,7 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *ou
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
                       uint32_t *out_dev, void *cuda_stream) {
   if (count > 0 && !out_dev) return HSGA_ERR_INVALID_ARG;
-  if (policy > HSGA_HYBRID || !power_of_two(S) || S < 2 || S > 64) return HSGA_ERR_INVALID_ARG;
+  if (policy > HSGA_HYBRID || !power_of_two(S) || S < 2 || S > 256) return HSGA_ERR_INVALID_ARG;
   if (policy == HSGA_HYBRID && S < 4) return HSGA_ERR_INVALID_ARG;
   if ((policy == HSGA_TILTED || policy == HSGA_STRETCHED) && (!power_of_two(W) || S / W < 2))
     return HSGA_ERR_INVALID_ARG;

@@ -169,6 +169,7 @@ struct RunParams {
   uint32_t bd32, bd_all;    // deleterious: otherwise w2 < floor(p_ben 2^32) + floor(p_del 2^32)
   uint32_t has_del;         // floor(p_del 2^32) > 0
   uint64_t vmask;          // (1 << bits) - 1
+  uint32_t words;          // surface width K in 64-bit words (S = 64 K / bits)
   uint32_t flt;            // binary32 fitness with Gaussian mutation amounts
   float gscale;            // float(sigma / sqrt(24 + 1/12) / 2^24)
   FastDiv cols_div;        // island -> (row, column)

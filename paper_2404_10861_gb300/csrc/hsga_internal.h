@@ -48,6 +48,23 @@ cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint
                           const uint64_t *s, uint32_t *out_words, uint32_t *out_is,
                           uint32_t *scratch, cudaStream_t stream, const uint32_t *T = nullptr);
 
+// Wide surfaces (hsga_wide.cu): the field(s) a synchronous generation
+// writes (word < 0: none).
+struct WideDeposit {
+  int word1;
+  uint32_t shift1;
+  int word2;
+  uint32_t shift2;
+};
+WideDeposit wide_deposit_for(const RunParams &p, uint64_t G);
+cudaError_t launch_migrate_wide(const RunParams &p, uint32_t G, uint32_t *t, uint64_t *s,
+                                uint64_t *rec, cudaStream_t stream);
+cudaError_t launch_step_wide(const RunParams &p, uint32_t G, const uint32_t *tin,
+                             const uint64_t *sin, uint32_t *tout, uint64_t *sout,
+                             cudaStream_t stream);
+cudaError_t launch_gather_wide(const RunParams &p, uint32_t G, uint32_t k, const uint32_t *t,
+                               const uint64_t *s, const uint32_t *where, uint32_t *out,
+                               cudaStream_t stream);
 cudaError_t launch_step_float(const RunParams &p, uint32_t G, const uint32_t *tin,
                               const uint64_t *sin, uint32_t *tout, uint64_t *sout,
                               cudaStream_t stream);

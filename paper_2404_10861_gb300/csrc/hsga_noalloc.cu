@@ -77,7 +77,8 @@ extern "C" int hsga_run_generations_noalloc(const hsga_config *cfg, uint64_t gen
                                             uint64_t *surf, void *cuda_stream) {
   const int v = validate_config(cfg);
   if (v != HSGA_OK) return v;
-  if (cfg->migration_mode != HSGA_MIGRATION_SYNC || cfg->fitness != HSGA_FITNESS_TRAIT)
+  if (cfg->migration_mode != HSGA_MIGRATION_SYNC || cfg->fitness != HSGA_FITNESS_TRAIT ||
+      cfg->surface_words > 1)
     return HSGA_ERR_UNSUPPORTED;
   const RunParams p = params_from_config(cfg);
   const bool tracked = cfg->surface_policy != HSGA_NONE;

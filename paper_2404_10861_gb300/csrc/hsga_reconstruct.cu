@@ -13,7 +13,8 @@
 // GPU formulation (all samples elapsed the same T, so they retain the same
 // deposition times):
 //   1. keys:  each surface's differentiae permuted into time order, oldest in
-//             the most significant bits, so that numeric order is path order;
+//             the most significant bits (of a key as wide as the surface), so
+//             that numeric order is path order;
 //   2. sort:  least-significant-digit radix sort of (key, sample) over the
 //             key's significant bits (8-bit digits; stable block scatter
 //             ranked with warp match);
@@ -45,22 +46,34 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
+constexpr int kMaxWords = 4;
+
 struct KeyPlan {
   uint32_t fields;     // retained differentiae m
   uint32_t bits;       // differentia width b
-  uint32_t src[64];    // bit offset of field j (time order) in the surface
+  uint32_t words;      // surface (and key) width K in 64-bit words
+  uint32_t src[64 * kMaxWords];  // bit offset of field j (time order) in the surface
+};
+
+// A key of K words: field j (time order) at key bits [j b, (j + 1) b)
+// counted from the most significant bit of word 0.
+struct KeyWords {
+  uint64_t *w[kMaxWords];
 };
 
 __global__ void make_keys_kernel(KeyPlan kp, const uint64_t *__restrict__ surf, uint32_t k,
-                                 uint64_t *__restrict__ key, uint32_t *__restrict__ val) {
+                                 KeyWords key, uint32_t *__restrict__ val) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= k) return;
-  const uint64_t s = surf[i];
   const uint64_t mask = (kp.bits == 64) ? ~0ull : ((1ull << kp.bits) - 1);
-  uint64_t out = 0;
-  for (uint32_t j = 0; j < kp.fields; ++j)
-    out |= ((s >> kp.src[j]) & mask) << (64u - (j + 1) * kp.bits);
-  key[i] = out;
+  uint64_t out[kMaxWords] = {0, 0, 0, 0};
+  for (uint32_t j = 0; j < kp.fields; ++j) {
+    const uint32_t src = kp.src[j];
+    const uint64_t v = (surf[(size_t)i * kp.words + src / 64] >> (src % 64)) & mask;
+    const uint32_t g = j * kp.bits;  // global key bit from the top
+    out[g / 64] |= v << (64u - g % 64 - kp.bits);
+  }
+  for (uint32_t w = 0; w < kp.words; ++w) key.w[w][i] = out[w];
   val[i] = i;
 }
 
@@ -68,6 +81,7 @@ __global__ void make_keys_kernel(KeyPlan kp, const uint64_t *__restrict__ surf, 
 __global__ void digit_histogram_kernel(const uint64_t *__restrict__ key, uint32_t k,
                                        uint32_t shift, uint32_t nblocks,
                                        uint32_t *__restrict__ hist) {
+  // key: the key word that holds this pass's digit
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -111,12 +125,10 @@ __global__ void exclusive_scan_kernel(uint32_t *__restrict__ a, uint32_t n,
 // digit.  A tile is processed in rounds of 256 elements; within a round the
 // rank of an element among equal digits is (earlier rounds) + (earlier
 // warps of this round) + (earlier lanes of its warp, from __match_any_sync).
-__global__ void digit_scatter_kernel(const uint64_t *__restrict__ key_in,
-                                     const uint32_t *__restrict__ val_in, uint32_t k,
-                                     uint32_t shift, uint32_t nblocks,
-                                     const uint32_t *__restrict__ offsets,
-                                     uint64_t *__restrict__ key_out,
-                                     uint32_t *__restrict__ val_out) {
+__global__ void digit_scatter_kernel(KeyWords key_in, const uint32_t *__restrict__ val_in,
+                                     uint32_t k, uint32_t words, uint32_t dword, uint32_t shift,
+                                     uint32_t nblocks, const uint32_t *__restrict__ offsets,
+                                     KeyWords key_out, uint32_t *__restrict__ val_out) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t running[256];
   __shared__ uint32_t wc[kWarps][256];
@@ -129,12 +141,12 @@ __global__ void digit_scatter_kernel(const uint64_t *__restrict__ key_in,
     const uint32_t e = base + r * kSortThreads + t;
     const bool live = e < k;
     const uint32_t active = __ballot_sync(0xFFFFFFFFu, live);
-    uint64_t kv = 0;
+    uint64_t kv[kMaxWords] = {0, 0, 0, 0};
     uint32_t vv = 0, d = 0, rank = 0;
     if (live) {
-      kv = key_in[e];
+      for (uint32_t w = 0; w < words; ++w) kv[w] = key_in.w[w][e];
       vv = val_in[e];
-      d = (uint32_t)(kv >> shift) & 0xFFu;
+      d = (uint32_t)(key_in.w[dword][e] >> shift) & 0xFFu;
       const uint32_t peers = __match_any_sync(active, d);
       rank = __popc(peers & ((1u << lane) - 1u));
       if (rank == 0) wc[warp][d] = __popc(peers);
@@ -152,7 +164,7 @@ __global__ void digit_scatter_kernel(const uint64_t *__restrict__ key_in,
     __syncthreads();
     if (live) {
       const uint32_t pos = wc[warp][d] + rank;
-      key_out[pos] = kv;
+      for (uint32_t w = 0; w < words; ++w) key_out.w[w][pos] = kv[w];
       val_out[pos] = vv;
     }
     __syncthreads();
@@ -160,12 +172,18 @@ __global__ void digit_scatter_kernel(const uint64_t *__restrict__ key_in,
 }
 
 // ----------------------------------------------------------------- lcp ---
-__global__ void lcp_kernel(const uint64_t *__restrict__ key, uint32_t k, uint32_t fields,
+__global__ void lcp_kernel(KeyWords key, uint32_t k, uint32_t words, uint32_t fields,
                            uint32_t bits, int32_t *__restrict__ L) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j + 1 >= k) return;
-  const uint64_t x = key[j] ^ key[j + 1];
-  const uint32_t same = x ? (uint32_t)__clzll((long long)x) / bits : fields;
+  uint32_t same = fields;
+  for (uint32_t w = 0; w < words; ++w) {
+    const uint64_t x = key.w[w][j] ^ key.w[w][j + 1];
+    if (x) {
+      same = (w * 64 + (uint32_t)__clzll((long long)x)) / bits;
+      break;
+    }
+  }
   L[j] = (int32_t)min(same, fields);
 }
 
@@ -306,19 +324,22 @@ inline uint32_t blocks_for(uint64_t n, uint32_t threads) {
 
 using namespace hsga;
 
-int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t policy, uint32_t differentia_bits,
-                     uint32_t W, uint64_t generations, uint32_t deposit_interval,
+int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t surface_words, uint32_t policy,
+                     uint32_t differentia_bits, uint32_t W, uint64_t generations,
+                     uint32_t deposit_interval,
                      int64_t *parent_out, int64_t *time_out, uint32_t *leaf_of_sample,
                      uint32_t capacity, uint32_t *n_nodes, void *cuda_stream) {
   const uint32_t b = differentia_bits;
   if (!surf || !parent_out || !time_out || !leaf_of_sample || !n_nodes) return HSGA_ERR_INVALID_ARG;
-  if (k == 0 || k > (1u << 28) || !(b == 1 || b == 2 || b == 4 || b == 8))
+  const uint32_t K = surface_words > 1 ? surface_words : 1;
+  if (k == 0 || k > (1u << 28) || !(b == 1 || b == 2 || b == 4 || b == 8 || b == 16))
     return HSGA_ERR_INVALID_ARG;
+  if (!(K == 1 || K == 2 || K == 4)) return HSGA_ERR_INVALID_ARG;
   if (policy > HSGA_HYBRID || policy == HSGA_NONE) return HSGA_ERR_INVALID_ARG;
   const uint64_t need_nodes = 2ull * k + 1;
   if (capacity < need_nodes) return HSGA_ERR_INVALID_ARG;
   // retained deposition times in ascending order (the same for every sample)
-  const uint32_t S = 64 / b;
+  const uint32_t S = 64 * K / b;
   const uint64_t kk = deposit_interval > 1 ? deposit_interval : 1;
   const uint64_t T = (generations + kk - 1) / kk;
   std::vector<int64_t> dep(S);
@@ -331,6 +352,7 @@ int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t policy, uint32_t
   KeyPlan kp{};
   kp.fields = (uint32_t)order.size();
   kp.bits = b;
+  kp.words = K;
   std::vector<int64_t> times(kp.fields > 0 ? kp.fields : 1, -1);
   for (uint32_t j = 0; j < kp.fields; ++j) {
     kp.src[j] = order[j] * b;
@@ -347,10 +369,12 @@ int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t policy, uint32_t
     held.push_back(p);
     return p;
   };
-  uint64_t *key[2] = {(uint64_t *)alloc(8ull * k), (uint64_t *)alloc(8ull * k)};
+  KeyWords key[2] = {};
+  for (int h = 0; h < 2; ++h)
+    for (uint32_t w = 0; w < K; ++w) key[h].w[w] = (uint64_t *)alloc(8ull * k);
   uint32_t *val[2] = {(uint32_t *)alloc(4ull * k), (uint32_t *)alloc(4ull * k)};
   uint32_t *hist = (uint32_t *)alloc(4ull * 256 * nblocks);
-  uint64_t *dsurf = (uint64_t *)alloc(8ull * k);
+  uint64_t *dsurf = (uint64_t *)alloc(8ull * k * K);
   int64_t *dtimes = (int64_t *)alloc(8ull * times.size());
   int32_t *L = (int32_t *)alloc(4ull * (n + 1));
   int32_t *ps = (int32_t *)alloc(4ull * (n + 1));
@@ -381,27 +405,29 @@ int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t policy, uint32_t
   cudaError_t e = cudaSuccess;
   uint32_t internal = 0;
   if (status == HSGA_OK) {
-    e = cudaMemcpyAsync(dsurf, surf, 8ull * k, cudaMemcpyDefault, st);
+    e = cudaMemcpyAsync(dsurf, surf, 8ull * k * K, cudaMemcpyDefault, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dtimes, times.data(), 8 * times.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
       make_keys_kernel<<<blocks_for(k, 256), 256, 0, st>>>(kp, dsurf, k, key[0], val[0]);
-      // sort over the significant bits only (the top fields * bits)
-      const uint32_t sig = kp.fields * b;
-      const uint32_t passes = (sig + 7) / 8;
+      // sort over the significant bits only (the top fields * bits, rounded
+      // up to whole 8-bit digits, which then never straddle two key words)
+      const uint32_t passes = (kp.fields * b + 7) / 8;
       int cur = 0;
       for (uint32_t ps_i = 0; ps_i < passes; ++ps_i) {
-        const uint32_t shift = 64 - 8 * passes + 8 * ps_i;
-        digit_histogram_kernel<<<nblocks, kSortThreads, 0, st>>>(key[cur], k, shift, nblocks, hist);
+        const uint32_t top = 8 * (passes - 1 - ps_i);  // digit's first bit from the top
+        const uint32_t dword = top / 64, shift = 64 - top % 64 - 8;
+        digit_histogram_kernel<<<nblocks, kSortThreads, 0, st>>>(key[cur].w[dword], k, shift,
+                                                                 nblocks, hist);
         exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, 256 * nblocks, nullptr);
-        digit_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(key[cur], val[cur], k, shift,
-                                                               nblocks, hist, key[1 - cur],
-                                                               val[1 - cur]);
+        digit_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(key[cur], val[cur], k, K, dword,
+                                                               shift, nblocks, hist,
+                                                               key[1 - cur], val[1 - cur]);
         cur = 1 - cur;
       }
       root_kernel<<<1, 1, 0, st>>>(dparent, dtime);
       if (n > 0) {
-        lcp_kernel<<<blocks_for(n, 256), 256, 0, st>>>(key[cur], k, kp.fields, b, L);
+        lcp_kernel<<<blocks_for(n, 256), 256, 0, st>>>(key[cur], k, K, kp.fields, b, L);
         for (int l = 1; l < mt.levels; ++l)
           min_level_kernel<<<blocks_for(mt.len[l], 256), 256, 0, st>>>(mt.lvl[l - 1],
                                                                        mt.len[l - 1], mt.lvl[l]);

@@ -40,7 +40,8 @@ def test_exports_every_declared_symbol(hb):
 def test_site_matches_oracle(hb, orc, policy):
     rng = np.random.default_rng(policy)
     Ts = list(range(5000)) + [int(x) for x in rng.integers(0, 2**32 - 2, 3000)]
-    for S, W in ((8, 2), (16, 4), (32, 2), (64, 2), (64, 1), (64, 4)):
+    for S, W in ((8, 2), (16, 4), (32, 2), (64, 2), (64, 1), (64, 4), (128, 2), (256, 2),
+                 (256, 4)):
         if policy == 5 and (S // 2) // W < 2:
             continue
         for T in Ts[::7]:
@@ -51,7 +52,8 @@ def test_site_matches_oracle(hb, orc, policy):
 def test_closed_form_lookup_matches_bruteforce(hb, orc, policy):
     """Timestamps are deduced from (site, T) alone; the closed form must equal
     the brute-force last-writer replay."""
-    for S, W in ((8, 2), (16, 2), (32, 2), (64, 2), (32, 4), (64, 4), (16, 1)):
+    for S, W in ((8, 2), (16, 2), (32, 2), (64, 2), (32, 4), (64, 4), (16, 1), (128, 2),
+                 (256, 2), (256, 4), (4, 1)):
         if policy == 5 and (S // 2) // W < 2:
             continue
         Ts = list(range(0, 600)) + [1023, 1024, 1025, 4095, 4096, 4097, 65535, 65536, 99999,
@@ -69,7 +71,9 @@ def test_config_validation_needs_no_gpu(hb):
            dict(policy="hybrid", bits=8, W=4), dict(policy=6),
            dict(fitness="float", sigma=0.0), dict(fitness="float", sigma=-1.0),
            dict(fitness="float", sigma=1.0, n=33), dict(mode="buffered", n=33),
-           dict(mode="buffered", coarsen=2)]
+           dict(mode="buffered", coarsen=2), dict(words=3), dict(words=8),
+           dict(words=2, n=33), dict(words=4, policy="none"), dict(bits=32),
+           dict(bits=16, policy="tilted", W=4)]
     for kw in bad:
         cfg = hb.make_config(**kw)
         out = ctypes.c_void_p()
