@@ -86,10 +86,7 @@ __device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, 
     child_t = mutate(p, fbest, w.z);
   const uint32_t Tp = fetch32<1>(pT, best);
   uint64_t child_s = 0;
-  if constexpr (TRACKED) {
-    const Deposit dep = deposit_unpack(deposit_pack(p, Tp), (uint32_t)p.vmask);
-    child_s = deposit_into<TWO>(dep, fetch64<1>(ps, best), w.w);
-  }
+  if constexpr (TRACKED) child_s = deposit_lane<TWO>(p, Tp, fetch64<1>(ps, best), w.w);
   t = child_t;
   s = child_s;
   T = Tp + 1u;

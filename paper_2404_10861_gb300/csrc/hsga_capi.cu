@@ -183,6 +183,8 @@ RunParams make_params(const hsga_config *c) {
   p.bd_all = thr_bd >= (1ull << 32) ? 1u : 0u;
   p.has_del = thr_bd > thr_ben ? 1u : 0u;
   p.vmask = (1ull << p.bits) - 1;
+  p.levels = p.S / p.W;
+  p.levels_half = (p.S / 2) / p.W;
   p.flt = c->fitness == HSGA_FITNESS_FLOAT ? 1u : 0u;
   p.gscale = p.flt ? (float)(c->mutation_sigma / sqrt(24.0 + 1.0 / 12.0) / 16777216.0) : 0.0f;
   p.cols_div = make_fastdiv(p.cols);

@@ -170,6 +170,7 @@ struct RunParams {
   uint32_t has_del;         // floor(p_del 2^32) > 0
   uint64_t vmask;          // (1 << bits) - 1
   uint32_t words;          // surface width K in 64-bit words (S = 64 K / bits)
+  uint32_t levels, levels_half;  // S / W and (S / 2) / W (tilted, stretched, hybrid half)
   uint32_t flt;            // binary32 fitness with Gaussian mutation amounts
   float gscale;            // float(sigma / sqrt(24 + 1/12) / 2^24)
   FastDiv cols_div;        // island -> (row, column)
@@ -345,6 +346,57 @@ __device__ __forceinline__ uint32_t mutate(const RunParams &p, uint32_t trait, u
   const uint32_t bd = (uint32_t)(w2 < p.bd32) | p.bd_all;
   const uint32_t dec = bd & (ben ^ 1u) & (uint32_t)(trait != 0u);
   return trait + inc - dec;
+}
+
+// Site of deposition T for one genome's own 32-bit counter (free-running
+// modes, T + 1 < 2^32): the functions of site_of in 32-bit arithmetic, with
+// the level counts precomputed; the steady policy defers to site_of.
+__device__ __forceinline__ uint32_t level_site32(bool tilted, uint32_t t1, uint32_t L, uint32_t W,
+                                                 uint32_t S) {
+  const uint32_t h = (uint32_t)__ffs((int)t1) - 1u;  // t1 > 0
+  uint32_t level, j;
+  if (h + 1u < L) {
+    level = h;
+    j = (uint32_t)((uint64_t)t1 >> (h + 1u));
+  } else {
+    level = L - 1u;
+    j = (uint32_t)((uint64_t)t1 >> (L - 1u)) - 1u;
+  }
+  if (tilted) return level * W + (j & (W - 1u));
+  return j < W ? level * W + j : S;
+}
+
+__device__ __forceinline__ uint32_t site_of32(const RunParams &p, uint32_t T) {
+  if (p.policy == HSGA_TILTED || p.policy == HSGA_STRETCHED)
+    return level_site32(p.policy == HSGA_TILTED, T + 1u, p.levels, p.W, p.S);
+  return site_of(p.policy, p.S, p.W, T);
+}
+
+// Writes the b-bit differentia v into site `site` (< S) of a 64-bit surface.
+__device__ __forceinline__ uint64_t put_site(uint64_t s, uint32_t site, uint32_t bits,
+                                             uint64_t vmask, uint32_t v) {
+  const uint32_t at = site * bits;
+  return (s & ~(vmask << at)) | (((uint64_t)v & vmask) << at);
+}
+
+// a6 for one genome with its own counter T: the site(s) of deposition T
+// (T / k when the coarsening interval k divides T, none otherwise), written
+// with word 3 of the child's block (bits 16.. for the hybrid tilted half).
+template <bool TWO>
+__device__ __forceinline__ uint64_t deposit_lane(const RunParams &p, uint32_t T, uint64_t s,
+                                                 uint32_t w3) {
+  if (p.coarsen > 1) {
+    if (T % p.coarsen) return s;
+    T /= p.coarsen;
+  }
+  const uint32_t a = site_of32(p, T);
+  if (a < p.S) s = put_site(s, a, p.bits, p.vmask, w3);
+  if constexpr (TWO) {
+    const uint32_t half = p.S >> 1;
+    const uint32_t b = level_site32(true, T + 1u, p.levels_half, p.W, half);
+    if (b < half) s = put_site(s, half + b, p.bits, p.vmask, w3 >> 16);
+  }
+  return s;
 }
 
 // Float fitness (hsga.h, HSGA_FITNESS_FLOAT): a later candidate wins only if
