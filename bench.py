@@ -515,12 +515,31 @@ def run_async_wafer(args, mode="async"):
         gens = steps * K
         out.append({"generations_per_launch": K, "generations": gens,
                     "value": AGENTS * gens / (ms / 1e3), "us_per_generation": ms * 1e3 / gens})
+    # Every genome streams through HBM each generation (the grid is far larger
+    # than what stays on chip): algorithmic bytes per agent-generation are the
+    # 16-byte genome (trait, surface, counter) read and written plus the
+    # exchange state per island spread over its agents (see the design notes);
+    # the ALU view counts 100 integer operations per replication (80 for the
+    # Philox4x32-10 block, the rest tournament, mutation and deposit).
+    best = max(out, key=lambda r: r["value"])
+    bytes_per_agent = {"async": 35.0, "buffered": 45.0}[mode]
+    peak, peak_kind = measured_peaks()
+    gbs = best["value"] * bytes_per_agent / 1e9
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = sms * 4 * 32 * 2070e6 / 1e12             # thread-ops/s, at the 2070 MHz maximum
+    alu = best["value"] * 100 / 1e12
     label = {"async": "free-running migration, latest-emigrant records",
              "buffered": "free-running migration, per-neighbour buffers"}[mode]
     print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
                       "workload": f"wafer-shaped island GA, {label} "
                                   "(512x1024 islands x 32 agents)",
-                      "config": dict(WORKLOAD, mode=mode), "slices": out, "dtype": "u32",
+                      "config": dict(WORKLOAD, mode=mode), "slices": out,
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                   "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
+                                   "algorithmic_bytes_per_agent_generation": bytes_per_agent},
+                      "alu": {"achieved": alu, "peak": alu_peak, "unit": "Tops/s",
+                              "frac": alu / alu_peak, "ops_per_replication": 100},
+                      "dtype": "u32",
                       "data": "synthetic"}), flush=True)
 
 

@@ -261,8 +261,13 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
   octet_step<TRACKED, T2, TWO, IPW, FLT>(p, o, lane, G);
 }
 
+// Residency bounds (blocks per SM) chosen by measurement at 16.8M agents:
+// more resident warps outweigh the few spilled registers.
+constexpr int kAsyncBlocksPerSM = 6;
+constexpr int kBufferedBlocksPerSM = 6;
+
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
-__global__ void __launch_bounds__(kResidentThreads)
+__global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
     step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                       uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
                       uint64_t *__restrict__ rec, uint32_t *__restrict__ seen_io,
@@ -433,7 +438,7 @@ __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IP
 }
 
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
-__global__ void __launch_bounds__(kResidentThreads)
+__global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
     step_buffered_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                          uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
                          uint64_t *__restrict__ mail, uint32_t *__restrict__ ack,
