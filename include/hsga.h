@@ -330,6 +330,15 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
+/* The counter-based generator every kernel draws from (Philox4x32-10 of
+ * Salmon et al., SC'11, key = (seed low, seed high)): out_dev[4 i + j] = word
+ * j of the block for counter (c0 + i, c1, c2, c3), i < count (c0 + count <=
+ * 2^32).  out_dev: device uint32.  Stream-ordered on cuda_stream.  For
+ * checking the generator against an independent implementation; the paper
+ * does not name its generator. */
+int hsga_philox_device(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1, uint32_t c2,
+                       uint32_t c3, uint32_t *out_dev, void *cuda_stream);
+
 /* Phylogeny reconstruction on the GPU from k sampled surfaces (of
  * surface_words 64-bit words each, agent-major; 0 means 1) that all
  * elapsed `generations` generations (synchronous mode, or free-running

@@ -134,6 +134,8 @@ def lib():
         _lib.orc_sample_grid.restype = ctypes.c_int
         _lib.orc_run_async.argtypes = [P(_Cfg), P(u32), P(u64), P(u32), u64, u32, P(u32)]
         _lib.orc_run_async.restype = ctypes.c_int
+        _lib.orc_philox_sweep.argtypes = [u64, u32, u32, u32, u32, u32, P(u32)]
+        _lib.orc_philox_sweep.restype = None
         _lib.orc_island_step.argtypes = [P(_Cfg), u32, u64, P(u32), P(u64), P(u32)]
         _lib.orc_island_step.restype = ctypes.c_int
         _lib.orc_run_buffered.argtypes = [P(_Cfg), P(u32), P(u64), P(u32), u64, u32, P(u32),
@@ -281,6 +283,13 @@ def run_async(cfg: Config, trait, surf, tcount, G0: int, generations: int, sched
     if rc != 0:
         raise MemoryError("oracle async run failed")
     return trait, surf, tcount
+
+
+def philox_sweep(seed: int, c0: int, count: int, c1: int, c2: int, c3: int) -> np.ndarray:
+    """Philox4x32-10 blocks for counters (c0 + i, c1, c2, c3): (count, 4) uint32."""
+    out = np.zeros((count, 4), dtype=np.uint32)
+    lib().orc_philox_sweep(seed, c0, count, c1, c2, c3, _p(out, ctypes.c_uint32))
+    return out
 
 
 def island_step(cfg: Config, island: int, G: int, trait, surf, tcount) -> None:

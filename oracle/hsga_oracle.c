@@ -102,6 +102,17 @@ ORC_PHILOX_DEFINE(orc_philox4x64_10, uint64_t, unsigned __int128, 64,
                   0xD2E7470EE14C6C93ull, 0xCA5A826395121157ull,
                   0x9E3779B97F4A7C15ull, 0xBB67AE8584CAA73Bull)
 
+/* Philox4x32-10 blocks for counters (c0 + i, c1, c2, c3), i < count, key
+ * (seed_lo, seed_hi): out[4 i + j] = word j (a bulk form of the generator,
+ * for sweeps in tests). */
+void orc_philox_sweep(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1,
+                      uint32_t c2, uint32_t c3, uint32_t *out) {
+  for (uint32_t i = 0; i < count; ++i) {
+    uint32_t ctr[4] = {c0 + i, c1, c2, c3};
+    orc_philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), ctr, out + 4 * (size_t)i);
+  }
+}
+
 /* floor(w * m / 2^32): a uniform index in [0, m) from one 32-bit word. */
 static uint32_t orc_index(uint32_t w, uint64_t m) {
   return (uint32_t)(((uint64_t)w * m) >> 32);

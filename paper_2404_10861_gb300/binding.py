@@ -92,6 +92,9 @@ _SIGS = {
     "hsga_get_async_log": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "hsga_get_migration_buffers": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
+    "hsga_philox_device": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p],
+                           ctypes.c_int),
     "hsga_reconstruct": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                           ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
                           ctypes.c_void_p,
@@ -305,6 +308,15 @@ def hsga_reconstruct(surf, policy, bits: int, W: int, generations: int, coarsen:
                                   ctypes.byref(nodes), s), "hsga_reconstruct")
     n = nodes.value
     return parent[:n], time[:n], leaf
+
+
+def hsga_philox_device(seed: int, c0: int, count: int, c1: int, c2: int, c3: int, out_dev,
+                       stream=None):
+    """Philox4x32-10 blocks for counters (c0 + i, c1, c2, c3) into a device
+    buffer of count x 4 uint32."""
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().hsga_philox_device(seed, c0, count, c1, c2, c3, _ptr(out_dev), s),
+           "hsga_philox_device")
 
 
 def hsga_synchronize(g):

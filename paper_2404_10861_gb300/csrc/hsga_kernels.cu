@@ -292,6 +292,27 @@ cudaError_t launch_sample(const RunParams &p, uint32_t G, uint32_t k, const uint
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ philox ---
+__global__ void philox_sweep_kernel(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t count,
+                                    uint32_t c1, uint32_t c2, uint32_t c3,
+                                    uint4 *__restrict__ out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += gridDim.x * blockDim.x) {
+    const Words4 w = philox(k0, k1, c0 + i, c1, c2, c3);
+    out[i] = make_uint4(w.x, w.y, w.z, w.w);
+  }
+}
+
+cudaError_t launch_philox_sweep(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1,
+                                uint32_t c2, uint32_t c3, uint32_t *out, cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  uint32_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  philox_sweep_kernel<<<blocks, 256, 0, stream>>>((uint32_t)seed, (uint32_t)(seed >> 32), c0,
+                                                  count, c1, c2, c3, (uint4 *)out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------- site function ---
 __global__ void sites_kernel(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                              uint64_t count, uint32_t *out) {

@@ -104,3 +104,27 @@ def test_philox_bits_and_index_uniform(orc):
     idx = (words * np.uint64(32)) >> np.uint64(32)
     counts = np.bincount(idx.astype(np.int64), minlength=32)
     assert stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_philox_sweep_matches_single_calls(orc):
+    key = 0x0123456789ABCDEF
+    for c0, c1, c2, c3 in [(0, 3, 5, 1), (2**32 - 64, 0xFFFFFFFF, 7, 0),
+                           (1000, 0xFFFFFFFE, 2**31, 256)]:
+        bulk = orc.philox_sweep(key, c0, 64, c1, c2, c3)
+        for i in range(64):
+            one = orc.philox4x32((key & 0xFFFFFFFF, key >> 32), (c0 + i, c1, c2, c3))
+            assert [int(x) for x in one] == bulk[i].tolist()
+
+
+def test_philox_uniform_over_2_to_24_words(orc):
+    """2^22 blocks (2^24 words): every bit ~ Bernoulli(1/2) within 5 sigma and
+    floor(w n / 2^32) uniform for n = 5, 32, 100 (chi-square)."""
+    from scipy import stats
+    w = orc.philox_sweep(1, 0, 1 << 22, 9, 11, 1).reshape(-1).astype(np.uint64)
+    sd = np.sqrt(0.25 / len(w))
+    for b in range(32):
+        f = ((w >> np.uint64(b)) & np.uint64(1)).mean()
+        assert abs(f - 0.5) < 5 * sd, b
+    for n in (5, 32, 100):
+        idx = ((w * np.uint64(n)) >> np.uint64(32)).astype(np.int64)
+        assert stats.chisquare(np.bincount(idx, minlength=n)).pvalue > 1e-4, n
