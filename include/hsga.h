@@ -330,6 +330,16 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
+/* The bounded wait the resident kernel applies to its neighbour flags, run
+ * by one GPU thread on a caller's flag: waits until *flag_dev >= seq, giving
+ * up after limit_ns (<= 1 s) of the GPU's global timer or 2^22 polls.
+ * Returns HSGA_OK when the flag arrived, HSGA_ERR_WAIT_TIMEOUT when the wait
+ * gave up (the context stays usable); *waited_ns (may be NULL) receives the
+ * time spent.  flag_dev: device uint32.  Synchronous on cuda_stream.  For
+ * checking that an unmet wait ends with a status instead of hanging. */
+int hsga_wait_probe(const uint32_t *flag_dev, uint32_t seq, uint64_t limit_ns,
+                    uint64_t *waited_ns, void *cuda_stream);
+
 /* The counter-based generator every kernel draws from (Philox4x32-10 of
  * Salmon et al., SC'11, key = (seed low, seed high)): out_dev[4 i + j] = word
  * j of the block for counter (c0 + i, c1, c2, c3), i < count (c0 + count <=

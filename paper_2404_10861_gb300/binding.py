@@ -92,6 +92,8 @@ _SIGS = {
     "hsga_get_async_log": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "hsga_get_migration_buffers": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
+    "hsga_wait_probe": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p], ctypes.c_int),
     "hsga_philox_device": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p],
                            ctypes.c_int),
@@ -308,6 +310,17 @@ def hsga_reconstruct(surf, policy, bits: int, W: int, generations: int, coarsen:
                                   ctypes.byref(nodes), s), "hsga_reconstruct")
     n = nodes.value
     return parent[:n], time[:n], leaf
+
+
+def hsga_wait_probe(flag_dev, seq: int, limit_ns: int, stream=None):
+    """Runs the resident kernel's bounded wait on a device flag; returns
+    (status, waited_ns) without raising on a timeout."""
+    waited = ctypes.c_uint64(0)
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    st = lib().hsga_wait_probe(_ptr(flag_dev), seq, limit_ns, ctypes.byref(waited), s)
+    if st not in (0, -5):
+        _check(st, "hsga_wait_probe")
+    return st, waited.value
 
 
 def hsga_philox_device(seed: int, c0: int, count: int, c1: int, c2: int, c3: int, out_dev,

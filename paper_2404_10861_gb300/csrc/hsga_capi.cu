@@ -909,6 +909,27 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *ou
   return HSGA_OK;
 }
 
+int hsga_wait_probe(const uint32_t *flag_dev, uint32_t seq, uint64_t limit_ns,
+                    uint64_t *waited_ns, void *cuda_stream) {
+  if (!flag_dev || limit_ns > 1000000000ull || !is_device_ptr(flag_dev))
+    return HSGA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  AllocHooks al = current_allocator();
+  void *scratch = device_alloc(al, 32, st);  // error word + two results
+  if (!scratch) return HSGA_ERR_OOM;
+  int *err = (int *)scratch;
+  uint64_t *out = (uint64_t *)((char *)scratch + 16);
+  uint64_t host[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 32, st);
+  if (e == cudaSuccess) e = launch_wait_probe(flag_dev, seq, limit_ns, err, out, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, out, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  device_free(al, scratch, st);
+  if (e != cudaSuccess) return HSGA_ERR_CUDA;
+  if (waited_ns) *waited_ns = host[1];
+  return host[0] ? HSGA_OK : HSGA_ERR_WAIT_TIMEOUT;
+}
+
 int hsga_philox_device(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1, uint32_t c2,
                        uint32_t c3, uint32_t *out_dev, void *cuda_stream) {
   if (count > 0 && (!out_dev || ((uintptr_t)out_dev % 16) != 0)) return HSGA_ERR_INVALID_ARG;

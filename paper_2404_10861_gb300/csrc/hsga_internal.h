@@ -92,6 +92,8 @@ bool device_pointer(const void *ptr);
 int validate_config(const hsga_config *c);
 RunParams params_from_config(const hsga_config *c);
 
+cudaError_t launch_wait_probe(const uint32_t *flag, uint32_t seq, uint64_t limit_ns, int *err,
+                              uint64_t *out, cudaStream_t stream);
 cudaError_t launch_philox_sweep(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1,
                                 uint32_t c2, uint32_t c3, uint32_t *out, cudaStream_t stream);
 cudaError_t launch_sites(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,

@@ -41,18 +41,33 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait until *flag >= seq.  Returns false on timeout or when
-// another warp already reported an error.
-__device__ bool wait_flag(const uint32_t *flag, uint32_t seq, const int *err) {
+// Bounded wait until *flag >= seq: gives up after limit_ns of the global
+// timer or kMaxSpins polls, whichever comes first, or as soon as another warp
+// has reported an error.  Returns false when it gave up.
+constexpr uint32_t kMaxSpins = 1u << 22;
+
+__device__ bool wait_flag(const uint32_t *flag, uint32_t seq, const int *err,
+                          uint64_t limit_ns = kWaitNs) {
   if (ld_acquire(flag) >= seq) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t spin = 1;; ++spin) {
+  for (uint32_t spin = 1; spin < kMaxSpins; ++spin) {
     if (ld_acquire(flag) >= seq) return true;
     if ((spin & 255u) == 0) {
       if (*(volatile const int *)err != 0) return false;
-      if (global_ns() - t0 > kWaitNs) return false;
+      if (global_ns() - t0 > limit_ns) return false;
     }
   }
+  return false;
+}
+
+// One thread runs wait_flag on a caller's flag (hsga_wait_probe): out[0] = 1
+// if the flag reached seq, 0 if the wait gave up; out[1] = nanoseconds spent.
+__global__ void wait_probe_kernel(const uint32_t *flag, uint32_t seq, uint64_t limit_ns,
+                                  int *err, uint64_t *out) {
+  const uint64_t t0 = global_ns();
+  const bool ok = wait_flag(flag, seq, err, limit_ns);
+  out[0] = ok ? 1u : 0u;
+  out[1] = global_ns() - t0;
 }
 
 // BLOCKSYNC: the whole grid lives in one thread block (at most 32 warps);
@@ -296,6 +311,12 @@ cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, u
   void *args[] = {&pp, &G0, &ngen, &prem, &t, &s, &rec, &flags, &err};
   return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.blocks),
                                      dim3(kResidentThreads), args, 0, stream);
+}
+
+cudaError_t launch_wait_probe(const uint32_t *flag, uint32_t seq, uint64_t limit_ns, int *err,
+                              uint64_t *out, cudaStream_t stream) {
+  wait_probe_kernel<<<1, 1, 0, stream>>>(flag, seq, limit_ns, err, out);
+  return cudaGetLastError();
 }
 
 }  // namespace hsga

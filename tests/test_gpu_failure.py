@@ -1,0 +1,50 @@
+"""Failure detection without a GPU fault: the bounded wait the resident
+kernel applies to neighbour flags, run on a flag that nothing sets, must end
+with HSGA_ERR_WAIT_TIMEOUT near its limit and leave the context usable; on a
+flag that is set it must return at once."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+WAIT_TIMEOUT = -5
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_10861_gb300 import _build, binding
+    _build.build()
+    return binding
+
+
+def test_unmet_wait_times_out_and_context_survives(hb, orc):
+    import torch
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    limit = 20_000_000                                      # 20 ms
+    status, waited = hb.hsga_wait_probe(flag, 1, limit)
+    assert status == WAIT_TIMEOUT
+    assert limit <= waited < limit + 200_000_000
+    flag.fill_(7)
+    status, waited = hb.hsga_wait_probe(flag, 3, limit)
+    assert status == 0 and waited < limit
+    # the context still runs kernels: a resident grid against the oracle
+    kw = dict(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, seed=1)
+    c = orc.Config(rows=4, cols=4, n=32, tournament=2, policy=orc.STEADY, bits=1, W=2,
+                   interval=1, seed=1)
+    want_t, want_s, _ = orc.run(c, generations=50)
+    with hb.Grid(kernel=hb.KERNEL_RESIDENT_GRID, **kw) as g:
+        g.run(50)
+        g.sync()
+        t, s = g.population()
+    assert np.array_equal(t, want_t) and np.array_equal(s, want_s)
+
+
+def test_probe_argument_checks(hb):
+    import torch
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(hb.HsgaError):
+        hb.hsga_wait_probe(flag, 1, 2_000_000_000)          # over the 1 s cap
+    with pytest.raises(hb.HsgaError):
+        hb.hsga_wait_probe(np.zeros(1, np.uint32), 1, 1000)  # host memory
