@@ -91,7 +91,7 @@ typedef enum hsga_kernel {
   HSGA_KERNEL_STREAMED = 1,  /* one launch per generation, population in HBM */
   HSGA_KERNEL_RESIDENT = 2,  /* persistent launch, genomes in registers; grids of at
                                 most 32 warps run in one block (block barriers), larger
-                                ones as a cooperative grid (neighbour flags) */
+                                ones as a cooperative grid (stamped neighbour records) */
   HSGA_KERNEL_RESIDENT_GRID = 3  /* resident, always the cooperative multi-block form */
 } hsga_kernel;
 
@@ -330,14 +330,16 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
-/* The bounded wait the resident kernel applies to its neighbour flags, run
- * by one GPU thread on a caller's flag: waits until *flag_dev >= seq, giving
- * up after limit_ns (<= 1 s) of the GPU's global timer or 2^22 polls.
- * Returns HSGA_OK when the flag arrived, HSGA_ERR_WAIT_TIMEOUT when the wait
- * gave up (the context stays usable); *waited_ns (may be NULL) receives the
- * time spent.  flag_dev: device uint32.  Synchronous on cuda_stream.  For
- * checking that an unmet wait ends with a status instead of hanging. */
-int hsga_wait_probe(const uint32_t *flag_dev, uint32_t seq, uint64_t limit_ns,
+/* The bounded wait the resident kernel applies to its neighbours' migrant
+ * records, run by one GPU thread on a caller's record: waits until all four
+ * 64-bit words of record_dev carry seq in their high 32 bits, giving up after
+ * limit_ns (<= 1 s) of the GPU's global timer or 2^22 polls.  Returns
+ * HSGA_OK when the record arrived, HSGA_ERR_WAIT_TIMEOUT when the wait gave
+ * up (the context stays usable); *waited_ns (may be NULL) receives the time
+ * spent.  record_dev: device, 4 uint64, 8-byte aligned.  Synchronous on
+ * cuda_stream.  For checking that an unmet wait ends with a status instead of
+ * hanging. */
+int hsga_wait_probe(const uint64_t *record_dev, uint32_t seq, uint64_t limit_ns,
                     uint64_t *waited_ns, void *cuda_stream);
 
 /* The counter-based generator every kernel draws from (Philox4x32-10 of
@@ -455,7 +457,7 @@ void hsga_batch_destroy(hsga_batch *b);
  *   generation: G of the population on entry (the result is at G + n).
  *   trait, surf: device planes, layout as hsga_set_population; surf may be
  *        NULL only for HSGA_NONE.  Host pointers are HSGA_ERR_INVALID_ARG.
- * Scratch (migrant records, sequence flags, error word: ~288 KiB) is one
+ * Scratch (stamped migrant records and an error word: ~512 KiB) is one
  * array built into the library and held on every device that loads it until
  * exit.  The first call on a device looks its address up
  * (cudaGetSymbolAddress), so make that first call before any stream capture.

@@ -40,8 +40,7 @@ struct hsga_grid {
   uint32_t *trait[2] = {nullptr, nullptr};
   uint64_t *surf[2] = {nullptr, nullptr};
   int cur = 0;
-  uint4 *rec = nullptr;      // 2 x islands migrant records
-  uint32_t *flags = nullptr; // islands
+  uint4 *rec = nullptr;      // migrant records, 64 B per island (two stamped 4-word slots)
   int *err = nullptr;        // device error word
   uint32_t *sample_scratch = nullptr;
   size_t sample_scratch_bytes = 0;
@@ -216,7 +215,6 @@ void free_grid(hsga_grid *g) {
   }
   dev_free(g->alloc, g->rec, g->stream);
   dev_free(g->alloc, g->wrec, g->stream);
-  dev_free(g->alloc, g->flags, g->stream);
   dev_free(g->alloc, g->err, g->stream);
   dev_free(g->alloc, g->sample_scratch, g->stream);
   dev_free(g->alloc, g->fossil_words, g->stream);
@@ -262,10 +260,9 @@ cudaError_t reset_channels(hsga_grid *g) {
 }
 
 int reset_sync_state(hsga_grid *g) {
-  cudaError_t e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t) * g->p.islands, g->stream);
+  // records of an earlier run must not carry an expected stamp
+  cudaError_t e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 4 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess) e = reset_channels(g);
-  if (e == cudaSuccess && g->async)
-    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess && g->seen)
     e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), g->stream);
@@ -321,7 +318,7 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
     g->surf[i] = tracked ? (uint64_t *)dev_alloc(g->alloc, sizeof(uint64_t) * g->swords, g->stream)
                          : nullptr;
   }
-  g->rec = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
+  g->rec = (uint4 *)dev_alloc(g->alloc, sizeof(uint4) * 4 * (size_t)g->p.islands, g->stream);
   g->async = cfg->migration_mode != HSGA_MIGRATION_SYNC;
   g->buffered = cfg->migration_mode == HSGA_MIGRATION_BUFFERED;
   if (g->async) {
@@ -353,9 +350,8 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
       return HSGA_ERR_OOM;
     }
   }
-  g->flags = (uint32_t *)dev_alloc(g->alloc, sizeof(uint32_t) * g->p.islands, g->stream);
   g->err = (int *)dev_alloc(g->alloc, sizeof(int), g->stream);
-  bool ok = g->trait[0] && g->trait[1] && g->rec && g->flags && g->err &&
+  bool ok = g->trait[0] && g->trait[1] && g->rec && g->err &&
             (!tracked || (g->surf[0] && g->surf[1]));
   if (!ok) {
     free_grid(g);
@@ -364,8 +360,6 @@ int hsga_init_grid(const hsga_config *cfg, void *cuda_stream, hsga_grid **out) {
   cudaError_t e = cudaMemsetAsync(g->trait[0], 0, sizeof(uint32_t) * g->agents, g->stream);
   if (e == cudaSuccess && tracked)
     e = cudaMemsetAsync(g->surf[0], 0, sizeof(uint64_t) * g->swords, g->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
   if (e != cudaSuccess || reset_sync_state(g) != HSGA_OK) {
     free_grid(g);
     return HSGA_ERR_CUDA;
@@ -509,7 +503,7 @@ int advance(hsga_grid *g, uint64_t n) {
       const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
       e = launch_step_resident(g->p, g->plan, (uint32_t)(g->G + done), m,
                                g->premigrated && done == 0, g->trait[g->cur], g->surf[g->cur],
-                               g->rec, g->flags, g->err, g->stream);
+                               reinterpret_cast<uint64_t *>(g->rec), g->err, g->stream);
       g->launches++;
       done += m;
     }
@@ -634,7 +628,7 @@ int hsga_set_async_log(hsga_grid *g, uint32_t generations) {
   cudaError_t e = cudaMemsetAsync(g->alog, 0, bytes, g->stream);
   // a fresh window: nothing published before it can be taken
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 2 * (size_t)g->p.islands, g->stream);
+    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 4 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(g->seen, 0, sizeof(uint32_t) * 4 * (size_t)g->p.islands, g->stream);
   if (e == cudaSuccess) e = reset_channels(g);
@@ -677,6 +671,10 @@ int hsga_migrate(hsga_grid *g) {
                           : launch_migrate(g->p, (uint32_t)g->G, g->trait[g->cur],
                                            g->surf[g->cur], g->rec, g->stream);
   g->launches += 2;
+  // the explicit records share the buffer with the resident kernel's stamped
+  // records: clear them so no stale word can carry an expected stamp
+  if (e == cudaSuccess && g->resident)
+    e = cudaMemsetAsync(g->rec, 0, sizeof(uint4) * 4 * (size_t)g->p.islands, g->stream);
   if (e != cudaSuccess) return HSGA_ERR_CUDA;
   g->premigrated = true;
   return HSGA_OK;
@@ -909,9 +907,10 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t N, int64_t *ou
   return HSGA_OK;
 }
 
-int hsga_wait_probe(const uint32_t *flag_dev, uint32_t seq, uint64_t limit_ns,
+int hsga_wait_probe(const uint64_t *record_dev, uint32_t seq, uint64_t limit_ns,
                     uint64_t *waited_ns, void *cuda_stream) {
-  if (!flag_dev || limit_ns > 1000000000ull || !is_device_ptr(flag_dev))
+  if (!record_dev || limit_ns > 1000000000ull || !is_device_ptr(record_dev) ||
+      ((uintptr_t)record_dev % 8) != 0)
     return HSGA_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   AllocHooks al = current_allocator();
@@ -921,7 +920,7 @@ int hsga_wait_probe(const uint32_t *flag_dev, uint32_t seq, uint64_t limit_ns,
   uint64_t *out = (uint64_t *)((char *)scratch + 16);
   uint64_t host[2] = {0, 0};
   cudaError_t e = cudaMemsetAsync(scratch, 0, 32, st);
-  if (e == cudaSuccess) e = launch_wait_probe(flag_dev, seq, limit_ns, err, out, st);
+  if (e == cudaSuccess) e = launch_wait_probe(record_dev, seq, limit_ns, err, out, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, out, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   device_free(al, scratch, st);

@@ -35,7 +35,7 @@ bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only = false
 
 cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
                                  uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
-                                 uint4 *rec, uint32_t *flags, int *err, cudaStream_t stream);
+                                 uint64_t *rec, int *err, cudaStream_t stream);
 
 cudaError_t launch_migrate(const RunParams &p, uint32_t G, uint32_t *t, uint64_t *s,
                            uint4 *rec, cudaStream_t stream);
@@ -92,7 +92,7 @@ bool device_pointer(const void *ptr);
 int validate_config(const hsga_config *c);
 RunParams params_from_config(const hsga_config *c);
 
-cudaError_t launch_wait_probe(const uint32_t *flag, uint32_t seq, uint64_t limit_ns, int *err,
+cudaError_t launch_wait_probe(const uint64_t *record, uint32_t seq, uint64_t limit_ns, int *err,
                               uint64_t *out, cudaStream_t stream);
 cudaError_t launch_philox_sweep(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1,
                                 uint32_t c2, uint32_t c3, uint32_t *out, cudaStream_t stream);

@@ -1,6 +1,6 @@
 // hsga_noalloc.cu -- hsga_run_generations_noalloc: the resident generation
-// kernel on caller-owned device planes, with its scratch memory (migrant
-// records, sequence flags, error word) in a fixed-size array that the
+// kernel on caller-owned device planes, with its scratch memory (stamped
+// migrant records, error word) in a fixed-size array that the
 // library image itself carries, so the call never allocates device memory.
 //
 // Who needs it: code that owns all device memory and forbids allocation
@@ -10,13 +10,13 @@
 // hsga_init_grid, which allocates the population planes and the scratch.
 //
 // The scratch array is a file-scope __device__ variable: every device that
-// loads the library holds it (kNoAllocScratchBytes, about 288 KiB) until the
+// loads the library holds it (kNoAllocScratchBytes, about 512 KiB) until the
 // process exits.  Its host-side name is only a stand-in for the device
 // address, so the address is looked up once per device with
 // cudaGetSymbolAddress (on the first call on that device, with that device
 // current) and passed to the kernel.  That first call should therefore come
 // before any stream capture.  All calls share the one array and it keeps the
-// last call's contents: each call clears the flags and the error word it
+// last call's contents: each call clears the records and the error word it
 // relies on, and calls whose work overlaps on the GPU race on it.
 #include <cuda_runtime.h>
 
@@ -29,9 +29,8 @@ namespace hsga {
 namespace {
 
 constexpr uint32_t kNoAllocMaxIslands = 8192;
-constexpr size_t kRecBytes = sizeof(uint4) * 2 * kNoAllocMaxIslands;   // 256 KiB
-constexpr size_t kFlagBytes = sizeof(uint32_t) * kNoAllocMaxIslands;   // 32 KiB
-constexpr size_t kNoAllocScratchBytes = kRecBytes + kFlagBytes + 256;  // + error word
+constexpr size_t kRecBytes = sizeof(uint64_t) * 8 * kNoAllocMaxIslands;  // 512 KiB
+constexpr size_t kNoAllocScratchBytes = kRecBytes + 256;                  // + error word
 constexpr uint64_t kNoAllocMaxGeneration = 0xFFFFFFFFull - 64;
 constexpr int kMaxDevices = 64;
 
@@ -92,19 +91,18 @@ extern "C" int hsga_run_generations_noalloc(const hsga_config *cfg, uint64_t gen
   unsigned char *scratch = nullptr;
   int r = scratch_address(&scratch);
   if (r != HSGA_OK) return r;
-  uint4 *rec = (uint4 *)scratch;
-  uint32_t *flags = (uint32_t *)(scratch + kRecBytes);
-  int *err = (int *)(scratch + kRecBytes + kFlagBytes);
+  uint64_t *rec = (uint64_t *)scratch;
+  int *err = (int *)(scratch + kRecBytes);
   cudaStream_t stream = (cudaStream_t)cuda_stream;
-  // the previous call's flags and error word must not leak into this one
-  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * p.islands, stream);
+  // the previous call's records and error word must not leak into this one
+  cudaError_t e = cudaMemsetAsync(rec, 0, sizeof(uint64_t) * 8 * p.islands, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), stream);
   const uint64_t slice = 1u << 16;
   for (uint64_t done = 0; done < n_generations && e == cudaSuccess;) {
     const uint32_t m =
         (uint32_t)((n_generations - done) < slice ? (n_generations - done) : slice);
     e = launch_step_resident(p, plan, (uint32_t)(generation + done), m, false, trait,
-                             tracked ? surf : nullptr, rec, flags, err, stream);
+                             tracked ? surf : nullptr, rec, err, stream);
     done += m;
   }
   int h = 0;

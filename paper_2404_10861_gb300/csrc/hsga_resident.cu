@@ -4,13 +4,18 @@
 // owns IPW islands and keeps their genomes in registers for the whole launch
 // (lane l: agents l and l+32).  There is no grid-wide barrier: islands only
 // depend on their four neighbours' emigrants, so each island publishes its
-// emigrant as a 16-byte record (one 128-bit store) into a slot double-
-// buffered by migration parity, then raises its sequence flag with a release
-// store; a receiver acquires the four neighbour flags before reading their
-// records.  An island can run at most one migration ahead of a neighbour,
-// which is why two record buffers suffice: a record of migration m is only
-// overwritten at m+2, after the writer has read the reader's m+1 record,
-// which the reader publishes only after it has consumed the m record.
+// emigrant as a record of four 64-bit words (trait, surface low, surface
+// high, direction), each word carrying the migration's sequence number in
+// its high half, into a slot double-buffered by migration parity; a
+// receiver polls the four words of each neighbour's record until all carry
+// the sequence number it expects.  A 64-bit relaxed access is single-copy
+// atomic, so no fence or separate flag is needed: seeing the number in all
+// four words means seeing the whole record.  An island can run at most one
+// migration ahead of a neighbour, which is why two record buffers suffice: a
+// record of migration m is only overwritten at m+2, after the writer has read
+// the reader's m+1 record, which the reader publishes only after its poll of
+// the m record has returned (the warp votes on the polled values before any
+// later store).
 //
 // Every wait is bounded (1 s of %globaltimer); on expiry the warp records a
 // timeout in the grid's error word and leaves, which lets its neighbours
@@ -25,14 +30,14 @@ namespace hsga {
 
 constexpr uint32_t kChunk = 16;  // generations whose per-island RNG blocks are batched
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed64(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -41,17 +46,29 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait until *flag >= seq: gives up after limit_ns of the global
-// timer or kMaxSpins polls, whichever comes first, or as soon as another warp
-// has reported an error.  Returns false when it gave up.
+// Bounded wait until all four words of a record carry sequence number seq
+// in their high halves; the record's low halves go to *out.  Gives up after
+// limit_ns of the global timer or kMaxSpins polls, whichever comes first, or
+// as soon as another warp has reported an error.  Returns false when it gave
+// up.
 constexpr uint32_t kMaxSpins = 1u << 22;
 
-__device__ bool wait_flag(const uint32_t *flag, uint32_t seq, const int *err,
-                          uint64_t limit_ns = kWaitNs) {
-  if (ld_acquire(flag) >= seq) return true;
+__device__ __forceinline__ bool record_ready(const uint64_t *r, uint32_t seq, uint4 *out) {
+  const uint64_t w0 = ld_relaxed64(r), w1 = ld_relaxed64(r + 1);
+  const uint64_t w2 = ld_relaxed64(r + 2), w3 = ld_relaxed64(r + 3);
+  if ((uint32_t)(w0 >> 32) != seq || (uint32_t)(w1 >> 32) != seq ||
+      (uint32_t)(w2 >> 32) != seq || (uint32_t)(w3 >> 32) != seq)
+    return false;
+  *out = make_uint4((uint32_t)w0, (uint32_t)w1, (uint32_t)w2, (uint32_t)w3);
+  return true;
+}
+
+__device__ bool wait_record(const uint64_t *r, uint32_t seq, const int *err, uint4 *out,
+                            uint64_t limit_ns = kWaitNs) {
+  if (record_ready(r, seq, out)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t spin = 1; spin < kMaxSpins; ++spin) {
-    if (ld_acquire(flag) >= seq) return true;
+    if (record_ready(r, seq, out)) return true;
     if ((spin & 255u) == 0) {
       if (*(volatile const int *)err != 0) return false;
       if (global_ns() - t0 > limit_ns) return false;
@@ -60,26 +77,27 @@ __device__ bool wait_flag(const uint32_t *flag, uint32_t seq, const int *err,
   return false;
 }
 
-// One thread runs wait_flag on a caller's flag (hsga_wait_probe): out[0] = 1
-// if the flag reached seq, 0 if the wait gave up; out[1] = nanoseconds spent.
-__global__ void wait_probe_kernel(const uint32_t *flag, uint32_t seq, uint64_t limit_ns,
+// One thread runs wait_record on a caller's record (hsga_wait_probe): out[0]
+// = 1 if the record carried seq, 0 if the wait gave up; out[1] = nanoseconds
+// spent.
+__global__ void wait_probe_kernel(const uint64_t *record, uint32_t seq, uint64_t limit_ns,
                                   int *err, uint64_t *out) {
   const uint64_t t0 = global_ns();
-  const bool ok = wait_flag(flag, seq, err, limit_ns);
+  uint4 r;
+  const bool ok = wait_record(record, seq, err, &r, limit_ns);
   out[0] = ok ? 1u : 0u;
   out[1] = global_ns() - t0;
 }
 
 // BLOCKSYNC: the whole grid lives in one thread block (at most 32 warps);
 // records go to shared memory and one __syncthreads per migration replaces
-// the flags (the record buffer of migration m is rewritten at m+2, after the
+// the record polling (the record buffer of migration m is rewritten at m+2, after the
 // barrier of m+1, which every reader of m has passed).
 template <int AP, int IPW, bool TRACKED, bool BLOCKSYNC>
 __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
     step_resident_kernel(RunParams p, uint32_t G0, uint32_t ngen, int premigrated,
                          uint32_t *__restrict__ tplane, uint64_t *__restrict__ splane,
-                         uint4 *__restrict__ rec, uint32_t *__restrict__ flags,
-                         int *__restrict__ err) {
+                         uint64_t *__restrict__ rec, int *__restrict__ err) {
   __shared__ uint4 srec[BLOCKSYNC ? 2 * 32 * IPW : 1];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -143,12 +161,16 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
                 sv = ps[k][1];
               }
             }
-            const uint4 r = make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
             if constexpr (BLOCKSYNC) {
-              srec[buf * 32 * IPW + isl[k]] = r;
+              srec[buf * 32 * IPW + isl[k]] =
+                  make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
             } else {
-              rec[(size_t)buf * p.islands + isl[k]] = r;
-              st_release(flags + isl[k], seq);
+              uint64_t *r = rec + ((size_t)buf * p.islands + isl[k]) * 4;
+              const uint64_t stamp = (uint64_t)seq << 32;
+              st_relaxed64(r, stamp | tv);
+              st_relaxed64(r + 1, stamp | (uint32_t)sv);
+              st_relaxed64(r + 2, stamp | (uint32_t)(sv >> 32));
+              st_relaxed64(r + 3, stamp | dir);
             }
           }
         }
@@ -170,8 +192,7 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
             if constexpr (BLOCKSYNC) {
               r = srec[buf * 32 * IPW + nb];
             } else {
-              ok = wait_flag(flags + nb, seq, err);
-              if (ok) r = __ldcg(rec + (size_t)buf * p.islands + nb);
+              ok = wait_record(rec + ((size_t)buf * p.islands + nb) * 4, seq, err, &r);
             }
             if (ok) {
               arrive = r.w == ((lane + 2u) & 3u);
@@ -225,8 +246,8 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
 }
 
 // ------------------------------------------------------------- launch ---
-using ResidentFn = void (*)(RunParams, uint32_t, uint32_t, int, uint32_t *, uint64_t *, uint4 *,
-                            uint32_t *, int *);
+using ResidentFn = void (*)(RunParams, uint32_t, uint32_t, int, uint32_t *, uint64_t *,
+                            uint64_t *, int *);
 
 static ResidentFn pick(int ap, int ipw, bool tracked, bool block) {
 #define HSGA_PICK(AP_, IPW_)                                                          \
@@ -299,23 +320,23 @@ bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
 
 cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
                                  uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
-                                 uint4 *rec, uint32_t *flags, int *err, cudaStream_t stream) {
+                                 uint64_t *rec, int *err, cudaStream_t stream) {
   ResidentFn fn = pick(plan.ap, plan.ipw, p.policy != HSGA_NONE, plan.block_sync);
   if (!fn) return cudaErrorInvalidValue;
   RunParams pp = p;
   int prem = premigrated ? 1 : 0;
   if (plan.block_sync) {
-    fn<<<1, plan.warps_per_block * 32, 0, stream>>>(pp, G0, ngen, prem, t, s, rec, flags, err);
+    fn<<<1, plan.warps_per_block * 32, 0, stream>>>(pp, G0, ngen, prem, t, s, rec, err);
     return cudaGetLastError();
   }
-  void *args[] = {&pp, &G0, &ngen, &prem, &t, &s, &rec, &flags, &err};
+  void *args[] = {&pp, &G0, &ngen, &prem, &t, &s, &rec, &err};
   return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.blocks),
                                      dim3(kResidentThreads), args, 0, stream);
 }
 
-cudaError_t launch_wait_probe(const uint32_t *flag, uint32_t seq, uint64_t limit_ns, int *err,
+cudaError_t launch_wait_probe(const uint64_t *record, uint32_t seq, uint64_t limit_ns, int *err,
                               uint64_t *out, cudaStream_t stream) {
-  wait_probe_kernel<<<1, 1, 0, stream>>>(flag, seq, limit_ns, err, out);
+  wait_probe_kernel<<<1, 1, 0, stream>>>(record, seq, limit_ns, err, out);
   return cudaGetLastError();
 }
 

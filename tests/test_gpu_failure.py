@@ -1,7 +1,8 @@
 """Failure detection without a GPU fault: the bounded wait the resident
-kernel applies to neighbour flags, run on a flag that nothing sets, must end
-with HSGA_ERR_WAIT_TIMEOUT near its limit and leave the context usable; on a
-flag that is set it must return at once."""
+kernel applies to its neighbours' stamped records, run on a record that
+nothing writes, must end with HSGA_ERR_WAIT_TIMEOUT near its limit and leave
+the context usable; on a record that carries the stamp it must return at
+once."""
 import numpy as np
 import pytest
 
@@ -21,14 +22,17 @@ def hb():
 
 def test_unmet_wait_times_out_and_context_survives(hb, orc):
     import torch
-    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    record = torch.zeros(4, dtype=torch.int64, device="cuda")
     limit = 20_000_000                                      # 20 ms
-    status, waited = hb.hsga_wait_probe(flag, 1, limit)
+    status, waited = hb.hsga_wait_probe(record, 1, limit)
     assert status == WAIT_TIMEOUT
     assert limit <= waited < limit + 200_000_000
-    flag.fill_(7)
-    status, waited = hb.hsga_wait_probe(flag, 3, limit)
+    record.copy_(torch.tensor([(3 << 32) | v for v in (11, 12, 13, 2)], dtype=torch.int64))
+    status, waited = hb.hsga_wait_probe(record, 3, limit)
     assert status == 0 and waited < limit
+    record[2] = (2 << 32) | 13                              # one word of an older record
+    status, _ = hb.hsga_wait_probe(record, 3, limit)
+    assert status == WAIT_TIMEOUT
     # the context still runs kernels: a resident grid against the oracle
     kw = dict(rows=4, cols=4, n=32, tournament=2, policy="steady", bits=1, seed=1)
     c = orc.Config(rows=4, cols=4, n=32, tournament=2, policy=orc.STEADY, bits=1, W=2,
@@ -43,8 +47,8 @@ def test_unmet_wait_times_out_and_context_survives(hb, orc):
 
 def test_probe_argument_checks(hb):
     import torch
-    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    record = torch.zeros(4, dtype=torch.int64, device="cuda")
     with pytest.raises(hb.HsgaError):
-        hb.hsga_wait_probe(flag, 1, 2_000_000_000)          # over the 1 s cap
+        hb.hsga_wait_probe(record, 1, 2_000_000_000)        # over the 1 s cap
     with pytest.raises(hb.HsgaError):
-        hb.hsga_wait_probe(np.zeros(1, np.uint32), 1, 1000)  # host memory
+        hb.hsga_wait_probe(np.zeros(4, np.uint64), 1, 1000)  # host memory
