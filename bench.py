@@ -418,6 +418,8 @@ def run_batched(args):
     _build.build()
     torch.cuda.set_device(0)
     hb.use_torch_allocator()
+    if args.gen_scale is None:
+        args.gen_scale = 100
     runs = batched_runs(args.gen_scale)
     reps = sum(g * kw["rows"] * kw["cols"] * kw["n"] for g, kw in runs)
     stream = torch.cuda.Stream()
@@ -463,6 +465,8 @@ def run_served(args):
     _build.build()
     torch.cuda.set_device(0)
     hb.use_torch_allocator()
+    if args.gen_scale is None:
+        args.gen_scale = 10
     rate = 20.0 * args.gen_scale      # keeps the offered load of the full-size stream
     reqs = serve.poisson_requests(args.requests, rate, seed=5, gen_scale=args.gen_scale)
     offered = sum(r.agents * r.generations for r in reqs) / reqs[-1].arrival
@@ -635,8 +639,9 @@ def main():
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--memory-cap-mb", type=int, default=2048,
                     help="served workload: device memory cap for admission")
-    ap.add_argument("--gen-scale", type=int, default=100,
-                    help="batched workload: divide the generation budgets by this")
+    ap.add_argument("--gen-scale", type=int, default=None,
+                    help="batched / served workloads: divide the generation budgets by this "
+                         "(default 100 batched, 10 served)")
     ap.add_argument("--slices", type=int, nargs="+", default=[1, 8, 64, 512],
                     help="async workload: generations per launch to measure")
     ap.add_argument("--async-gens", type=int, default=2048,
