@@ -376,10 +376,19 @@ def run_secondary(args):
                     "value": agents * gens * args.steps / (ms / 1e3),
                     "ms_per_step": ms / args.steps, "us_per_generation": ms * 1e3 / (gens * args.steps),
                     "islands_per_warp": st["islands_per_warp"], "blocks": st["blocks"]})
+    # the resident path's roofline is integer issue: 100 operations per
+    # replication against 152 SMs x 4 schedulers x 32 lanes at 2,070 MHz
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = sms * 4 * 32 * 2070e6 / 1e12
+    best = max(out, key=lambda r: r["value"])
+    alu = best["value"] * 100 / 1e12
     print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
                       "workload": args.workload, "config": dict(kw, generations_per_step=gens),
                       "steps": args.steps, "warmup": args.warmup, "dtype": "u32",
-                      "data": "synthetic", "kernels": out}), flush=True)
+                      "data": "synthetic", "kernels": out,
+                      "alu": {"kernel": best["kernel"], "achieved": alu, "peak": alu_peak,
+                              "unit": "Tops/s", "frac": alu / alu_peak,
+                              "ops_per_replication": 100}}), flush=True)
 
 
 def splitmix64(x: int) -> int:
