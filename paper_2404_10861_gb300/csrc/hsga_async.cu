@@ -264,7 +264,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
 // Residency bounds (blocks per SM) chosen by measurement at 16.8M agents:
 // more resident warps outweigh the few spilled registers.
 constexpr int kAsyncBlocksPerSM = 6;
-constexpr int kBufferedBlocksPerSM = 6;
+constexpr int kBufferedBlocksPerSM = 8;
 
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
 __global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
@@ -476,7 +476,10 @@ __global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
   }
 }
 
+// Islands per warp, chosen by measurement at 16.8M agents: the buffered
+// kernel's larger per-lane state favours shorter octets and more warps.
 constexpr int kAsyncIslandsPerWarp = 8;
+constexpr int kBufferedIslandsPerWarp = 4;
 
 using AsyncFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
                          uint64_t *, uint32_t *, uint32_t *, uint32_t, uint32_t);
@@ -503,7 +506,7 @@ using BufferedFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t 
                             uint32_t);
 
 BufferedFn pick_buffered(bool tracked, bool t2, bool two, bool flt) {
-  constexpr int I = kAsyncIslandsPerWarp;
+  constexpr int I = kBufferedIslandsPerWarp;
   if (flt) {  // general tournament path only
     if (!tracked) return step_buffered_kernel<false, false, false, I, true>;
     return two ? step_buffered_kernel<true, false, true, I, true>
@@ -562,9 +565,9 @@ constexpr int kFloatIslandsPerWarp = 4;
 // Blocks for a free-running launch: one warp per octet, but never more
 // blocks than the device keeps resident at once, so that every island
 // advances in the same pass over the grid (warps then own several octets).
-uint32_t resident_blocks(const void *fn, uint32_t islands) {
+uint32_t resident_blocks(const void *fn, uint32_t islands, uint32_t ipw) {
   const uint32_t wpb = kResidentThreads / 32;
-  const uint32_t octets = (islands + kAsyncIslandsPerWarp - 1) / kAsyncIslandsPerWarp;
+  const uint32_t octets = (islands + ipw - 1) / ipw;
   const uint32_t need = (octets + wpb - 1) / wpb;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -602,7 +605,7 @@ cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen,
                                  uint32_t log_gens, cudaStream_t stream) {
   BufferedFn fn =
       pick_buffered(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
-  const uint32_t blocks = resident_blocks((const void *)fn, p.islands);
+  const uint32_t blocks = resident_blocks((const void *)fn, p.islands, kBufferedIslandsPerWarp);
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, mail, ack, inbuf, chst, log,
                                                log_G0, log_gens);
   return cudaGetLastError();
@@ -614,7 +617,7 @@ cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, ui
                               cudaStream_t stream) {
   AsyncFn fn =
       pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
-  const uint32_t blocks = resident_blocks((const void *)fn, p.islands);
+  const uint32_t blocks = resident_blocks((const void *)fn, p.islands, kAsyncIslandsPerWarp);
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, rec, seen, log, log_G0,
                                                log_gens);
   return cudaGetLastError();
