@@ -131,9 +131,10 @@ __device__ __forceinline__ void land(uint32_t slot, uint32_t src, uint32_t it, u
 // evaluates the emigrant block of the neighbour in direction r of island
 // isl0+p and gathers that emigrant's genome from the parent planes when it is
 // aimed at isl0+p; lane 5p+4 evaluates the placement block of isl0+p and
-// turns it into a landing plan: byte d holds the slot where the direction-d
-// immigrant ends up, or 0xFF when it does not arrive or a later direction
-// lands on the same slot (later arrivals overwrite earlier ones).
+// turns it into a landing plan: byte 3-d holds the slot where the direction-d
+// immigrant lands, or 0xFF when it does not arrive.  Later arrivals overwrite
+// earlier ones, and the reversed byte order makes the lowest matching byte
+// the latest direction, so slots shared by several arrivals need no pass.
 constexpr uint32_t kGroup = 6;  // 6 islands x 5 blocks = 30 of 32 lanes
 
 struct GroupMigration {
@@ -164,17 +165,14 @@ __device__ __forceinline__ void group_migration(const RunParams &p, uint32_t isl
   }
   const uint32_t arrivals = __ballot_sync(kFull, arrive);
   const uint32_t bits = (arrivals >> (5u * pi)) & 0xFu;
-  uint32_t b[4] = {uindex(m.x, p.n), uindex(m.y, p.n), uindex(m.z, p.n), uindex(m.w, p.n)};
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    if (!((bits >> d) & 1u)) b[d] = 0xFFu;
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int e = d + 1; e < 4; ++e)
-      if (b[e] == b[d]) b[d] = 0xFFu;
-  gm.plan = (role == 4 && valid) ? (b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24))
-                                 : 0xFFFFFFFFu;
+  // slots (< 64) in byte d, 0xFF in the bytes of directions with no arrival
+  // (the multiply spreads bit d of `miss` to bit 8d without carries), then the
+  // byte order reversed
+  const uint32_t miss = ~bits & 0xFu;
+  const uint32_t fwd = uindex(m.x, p.n) | (uindex(m.y, p.n) << 8) | (uindex(m.z, p.n) << 16) |
+                       (uindex(m.w, p.n) << 24) |
+                       (((miss * 0x00204081u) & 0x01010101u) * 0xFFu);
+  gm.plan = (role == 4 && valid) ? __byte_perm(fwd, 0u, 0x0123u) : 0xFFFFFFFFu;
 }
 
 // a2 for island isl0+k: each lane looks its slots up in the landing plan
@@ -189,10 +187,11 @@ __device__ __forceinline__ void group_land(const GroupMigration &gm, uint32_t k,
 #pragma unroll
   for (int a = 0; a < AP; ++a) {
     const uint32_t x = plan ^ ((lane + 32u * a) * 0x01010101u);
-    // lowest zero byte of x (at most one byte can match: plan bytes of
-    // surviving directions are distinct)
+    // the lowest set bit of z marks the lowest zero byte of x exactly (a
+    // borrow only runs upward from a zero byte); byte 3-d is direction d, so
+    // bit 31-8d isolated has 8d leading zeros
     const uint32_t z = (x - 0x01010101u) & ~x & 0x80808080u;
-    const uint32_t d = (uint32_t)(__ffs(z) - 1) >> 3;
+    const uint32_t d = (uint32_t)__clz(z & (0u - z)) >> 3;
     const uint32_t src = z ? 5u * k + d : lane;
     const uint32_t vt = __shfl_sync(kFull, gm.it, src);
     if (z) pt[a] = vt;
@@ -248,8 +247,11 @@ __device__ __forceinline__ void store_island(const RunParams &p, uint32_t isl,
 // parallelism hides the multiply-xor dependency chain of the rounds).
 constexpr int kInterleave = 2;
 
+// MIG: 1 or 0 when the launch is known to migrate or not (the migration draws
+// then share a basic block with the first islands' replication draws, and the
+// scheduler interleaves the chains); -1 reads do_mig at run time.
 template <int AP, bool TRACKED, bool T2, int NN, int ILV = kInterleave, bool RK = true,
-          bool TWO = false, bool DEL = true>
+          bool TWO = false, bool DEL = true, int MIG = -1>
 __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &dep, uint32_t G,
                                            bool do_mig, uint32_t isl0,
                                            const uint32_t *__restrict__ tin,
@@ -258,6 +260,7 @@ __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &de
                                            uint64_t *__restrict__ sout,
                                            const PhiloxHead (&head)[AP]) {
   static_assert(kGroup % ILV == 0, "interleave width must divide the group");
+  if constexpr (MIG >= 0) do_mig = MIG == 1;
   uint32_t pt[kGroup][AP];
   uint64_t ps[kGroup][AP];
 #pragma unroll

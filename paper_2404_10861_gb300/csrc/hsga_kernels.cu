@@ -18,11 +18,14 @@ namespace hsga {
 // ------------------------------------------------------ streamed step ---
 // The group helpers (migration draws, landing plans, island loads/stores)
 // live in hsga_island.cuh.
-template <int AP, bool TRACKED, bool T2, int NN>
+// MIG: whether this generation migrates (a compile-time flag, so that the
+// full groups carry no run-time branch around the migration draws).
+template <int AP, bool TRACKED, bool T2, int NN, bool MIG>
 __global__ void __launch_bounds__(kStreamThreads, AP == 1 ? kStreamBlocksPerSM : 1)
-    step_streamed_kernel(RunParams p, Deposit dep, uint32_t G, int do_mig,
+    step_streamed_kernel(RunParams p, Deposit dep, uint32_t G,
                          const uint32_t *__restrict__ tin, const uint64_t *__restrict__ sin,
                          uint32_t *__restrict__ tout, uint64_t *__restrict__ sout) {
+  constexpr int M = MIG ? 1 : 0;
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
   const uint32_t ngroups = (p.islands + kGroup - 1) / kGroup;
@@ -32,29 +35,29 @@ __global__ void __launch_bounds__(kStreamThreads, AP == 1 ? kStreamBlocksPerSM :
     const uint32_t isl0 = grp * kGroup;
     if (isl0 + kGroup <= p.islands) {
       if (dep.two)
-        full_group<AP, TRACKED, T2, NN, kInterleave, true, true>(p, dep, G, do_mig != 0, isl0,
-                                                                 tin, sin, tout, sout, head);
+        full_group<AP, TRACKED, T2, NN, kInterleave, true, true, true, M>(
+            p, dep, G, MIG, isl0, tin, sin, tout, sout, head);
       else if (p.has_del)
-        full_group<AP, TRACKED, T2, NN>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout,
-                                        head);
+        full_group<AP, TRACKED, T2, NN, kInterleave, true, false, true, M>(
+            p, dep, G, MIG, isl0, tin, sin, tout, sout, head);
       else
-        full_group<AP, TRACKED, T2, NN, kInterleave, true, false, false>(
-            p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout, head);
+        full_group<AP, TRACKED, T2, NN, kInterleave, true, false, false, M>(
+            p, dep, G, MIG, isl0, tin, sin, tout, sout, head);
     }
     else
-      partial_group<AP, TRACKED, T2>(p, dep, G, do_mig != 0, isl0, tin, sin, tout, sout);
+      partial_group<AP, TRACKED, T2>(p, dep, G, MIG, isl0, tin, sin, tout, sout);
   }
 }
 
-template <int AP, bool TRACKED, bool T2, int NN>
+template <int AP, bool TRACKED, bool T2, int NN, bool MIG>
 static int streamed_blocks() {
   static int blocks = 0;
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_streamed_kernel<AP, TRACKED, T2, NN>,
-                                                  kStreamThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, step_streamed_kernel<AP, TRACKED, T2, NN, MIG>, kStreamThreads, 0);
     blocks = sms * (per_sm > 0 ? per_sm : 1);
   }
   return blocks;
@@ -66,10 +69,15 @@ static void launch_streamed_t(const RunParams &p, const Deposit &dep, uint32_t G
                               uint64_t *sout, cudaStream_t stream) {
   const uint32_t groups = (p.islands + kGroup - 1) / kGroup;
   const uint32_t need = (groups + kStreamThreads / 32 - 1) / (kStreamThreads / 32);
-  int b = streamed_blocks<AP, TRACKED, T2, NN>();
+  int b = do_mig ? streamed_blocks<AP, TRACKED, T2, NN, true>()
+                 : streamed_blocks<AP, TRACKED, T2, NN, false>();
   if ((uint32_t)b > need) b = (int)need;
-  step_streamed_kernel<AP, TRACKED, T2, NN>
-      <<<b, kStreamThreads, 0, stream>>>(p, dep, G, do_mig ? 1 : 0, tin, sin, tout, sout);
+  if (do_mig)
+    step_streamed_kernel<AP, TRACKED, T2, NN, true>
+        <<<b, kStreamThreads, 0, stream>>>(p, dep, G, tin, sin, tout, sout);
+  else
+    step_streamed_kernel<AP, TRACKED, T2, NN, false>
+        <<<b, kStreamThreads, 0, stream>>>(p, dep, G, tin, sin, tout, sout);
 }
 
 cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
