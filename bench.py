@@ -68,29 +68,33 @@ KERNEL_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",
                   "paper_2404_10861_gb300/csrc/hsga_island.cuh",
                   "paper_2404_10861_gb300/csrc/hsga_kernels.cu"]
 PROFILE = os.path.join(ROOT, "profiles", "step_streamed_wafer.md")
+FREE_RUNNING_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",
+                        "paper_2404_10861_gb300/csrc/hsga_island.cuh",
+                        "paper_2404_10861_gb300/csrc/hsga_async.cu"]
+FREE_RUNNING_PROFILE = os.path.join(ROOT, "profiles", "step_free_running_wafer.md")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the streamed kernel from the committed ncu
-    summary, or None when the kernel sources changed since that capture."""
+def profiled_traffic(key="dram_bytes_per_launch", profile=PROFILE, sources=KERNEL_SOURCES):
+    """DRAM bytes (the `key` field) from a committed ncu summary, or None when
+    the kernel sources changed since that capture."""
     try:
         fields = {}
-        for line in open(PROFILE):
-            if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch")):
+        for line in open(profile):
+            if ":" in line and line.strip().startswith(("source_sha256", key)):
                 k, v = line.strip().strip("`").split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
-        if fields.get("source_sha256") != kernel_source_hash():
+        if fields.get("source_sha256") != kernel_source_hash(sources):
             return None
-        return int(fields["dram_bytes_per_launch"])
+        return int(fields[key])
     except Exception:
         return None
 
@@ -500,11 +504,11 @@ def run_served(args):
 
 
 def run_async_wafer(args, mode="async"):
-    """Free-running migration on the wafer-shaped grid, advanced in slices of
-    K generations per launch (each island is loaded once and stored once per
-    slice; within a slice islands never wait for one another).  mode "async":
-    latest-emigrant records; "buffered": the per-neighbour send and receive
-    buffers."""
+    """Free-running migration on the wafer-shaped grid, K generations per
+    persistent launch (every warp stays resident and streams its islands
+    through HBM each generation; islands never wait for one another).  mode
+    "async": latest-emigrant records; "buffered": the per-neighbour send and
+    receive buffers."""
     import torch
     from paper_2404_10861_gb300 import _build, binding as hb
     _build.build()
@@ -543,12 +547,19 @@ def run_async_wafer(args, mode="async"):
     alu = best["value"] * 100 / 1e12
     label = {"async": "free-running migration, latest-emigrant records",
              "buffered": "free-running migration, per-neighbour buffers"}[mode]
+    # DRAM traffic from the committed ncu capture (bytes per generation; a
+    # launch of K generations streams the grid K times)
+    per_gen = profiled_traffic(f"{mode}_dram_bytes_per_generation", FREE_RUNNING_PROFILE,
+                               FREE_RUNNING_SOURCES)
+    traffic = per_gen * best["generations_per_launch"] if per_gen is not None else None
     print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
                       "workload": f"wafer-shaped island GA, {label} "
                                   "(512x1024 islands x 32 agents)",
                       "config": dict(WORKLOAD, mode=mode), "slices": out,
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                                   "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
+                                   "frac": gbs / peak, "traffic": traffic,
+                                   "traffic_per_generation": per_gen, "peak_kind": peak_kind,
+                                   "generations_per_launch": best["generations_per_launch"],
                                    "algorithmic_bytes_per_agent_generation": bytes_per_agent},
                       "alu": {"achieved": alu, "peak": alu_peak, "unit": "Tops/s",
                               "frac": alu / alu_peak, "ops_per_replication": 100},

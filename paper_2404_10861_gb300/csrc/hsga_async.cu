@@ -44,15 +44,16 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
 // a3-a6 of one island (lane = child slot) when genomes carry their own
 // deposition counters: the child deposits at site(T_parent) and carries
 // T_parent + 1.  t, s, T: this lane's genome, replaced by its child.  FLT:
-// binary32 fitness with Gaussian mutation amounts.
+// binary32 fitness with Gaussian mutation amounts.  h: the head of the
+// replication block Philox(key; lane, *, G, 1), shared by all islands.
 template <bool TRACKED, bool T2, bool TWO, bool FLT = false>
-__device__ __forceinline__ void counter_step(const RunParams &p, uint32_t lane, uint32_t isl,
-                                             uint32_t G, uint32_t &t, uint64_t &s,
-                                             uint32_t &T) {
+__device__ __forceinline__ void counter_step(const RunParams &p, const PhiloxHead &h,
+                                             uint32_t lane, uint32_t isl, uint32_t G,
+                                             uint32_t &t, uint64_t &s, uint32_t &T) {
   const uint32_t n = p.n;
   uint32_t pt[1] = {t}, pT[1] = {T};
   uint64_t ps[1] = {s};
-  const Words4 w = philox_rk(p, lane, isl, G, kPurposeReplicate);
+  const Words4 w = philox_tail<true>(p, h, isl);
   uint32_t best = uindex(w.x, n);
   uint32_t fbest = fetch32<1>(pt, best);
   if (T2 || p.tournament >= 2) {
@@ -158,14 +159,17 @@ __device__ __forceinline__ void store_octet(const RunParams &p, const Octet<IPW>
   }
 }
 
-// a3-a6 for every island of the octet
+// a3-a6 for every island of the octet.  Islands past the end of the grid
+// (last octet only) hold zeros that are never stored or published, so they
+// are stepped too: with no branch per island the islands' Philox chains
+// share one basic block and the scheduler interleaves them.
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
 __device__ __forceinline__ void octet_step(const RunParams &p, Octet<IPW> &o, uint32_t lane,
                                            uint32_t G) {
+  const PhiloxHead h = philox_head(p.k0, p.k1, lane, G, kPurposeReplicate);
 #pragma unroll
   for (int k = 0; k < IPW; ++k)
-    if (o.live[k])
-      counter_step<TRACKED, T2, TWO, FLT>(p, lane, o.first + k, G, o.t[k], o.s[k], o.T[k]);
+    counter_step<TRACKED, T2, TWO, FLT>(p, h, lane, o.first + k, G, o.t[k], o.s[k], o.T[k]);
 }
 
 // Octets owned by this warp: warp, warp + nwarps, ...
@@ -263,7 +267,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
 
 // Residency bounds (blocks per SM) chosen by measurement at 16.8M agents:
 // more resident warps outweigh the few spilled registers.
-constexpr int kAsyncBlocksPerSM = 6;
+constexpr int kAsyncBlocksPerSM = 8;
 constexpr int kBufferedBlocksPerSM = 8;
 
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
@@ -476,9 +480,9 @@ __global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
   }
 }
 
-// Islands per warp, chosen by measurement at 16.8M agents: the buffered
-// kernel's larger per-lane state favours shorter octets and more warps.
-constexpr int kAsyncIslandsPerWarp = 8;
+// Islands per warp, chosen by measurement at 16.8M agents: four-island
+// octets at 8 blocks per SM beat eight-island octets at 6 in both modes.
+constexpr int kAsyncIslandsPerWarp = 4;
 constexpr int kBufferedIslandsPerWarp = 4;
 
 using AsyncFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
@@ -548,11 +552,12 @@ __global__ void __launch_bounds__(kResidentThreads)
       if constexpr (TRACKED) s[k] = sin[isl * n + lane];
     }
   }
+  const PhiloxHead h = philox_head(p.k0, p.k1, lane, G, kPurposeReplicate);
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
     const uint32_t isl = first + k;
     if (isl >= p.islands) break;
-    counter_step<TRACKED, false, TWO, true>(p, lane, isl, G, t[k], s[k], T[k]);
+    counter_step<TRACKED, false, TWO, true>(p, h, lane, isl, G, t[k], s[k], T[k]);
     if (lane < n) {
       tout[isl * n + lane] = t[k];
       if constexpr (TRACKED) sout[isl * n + lane] = s[k];
