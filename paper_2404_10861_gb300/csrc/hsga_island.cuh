@@ -58,12 +58,19 @@ __device__ __forceinline__ void replication_words(const RunParams &p, uint32_t i
     w[a] = philox_p<RK>(p, lane + 32u * a, isl, G, kPurposeReplicate);
 }
 
+// floor(w n / 2^32); NN: n when known at compile time (32: a shift), else 0.
+template <int NN>
+__device__ __forceinline__ uint32_t uindex_nn(uint32_t w, uint32_t n) {
+  if constexpr (NN == 32) return w >> 27;
+  else return uindex(w, n);
+}
+
 // a3-a6 for one island: parents (pt, ps) -> children (ct, cs).  Every lane
 // runs the same shuffles; children of lanes at or beyond n are garbage and
 // are never stored.  Candidate indices are always < n, so only loaded
 // parents are ever read.  T2: the tournament size is exactly 2.
 template <int AP, bool TRACKED, bool T2 = false, bool RK = true, bool TWO = false,
-          bool DEL = true>
+          bool DEL = true, int NN = 0>
 __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep, uint32_t isl,
                                           uint32_t G, const Words4 (&w)[AP],
                                           const uint32_t (&pt)[AP], const uint64_t (&ps)[AP],
@@ -73,10 +80,10 @@ __device__ __forceinline__ void replicate(const RunParams &p, const Deposit &dep
   for (int a = 0; a < AP; ++a) {
     // a3 + a4: fitness is the trait; tournament with replacement, the first
     // drawn candidate keeps ties.
-    uint32_t best = uindex(w[a].x, n);
+    uint32_t best = uindex_nn<NN>(w[a].x, n);
     uint32_t fbest = fetch32<AP>(pt, best);
     if (T2 || p.tournament >= 2) {
-      const uint32_t c = uindex(w[a].y, n);
+      const uint32_t c = uindex_nn<NN>(w[a].y, n);
       const uint32_t fc = fetch32<AP>(pt, c);
       const bool take = fc > fbest;
       best = take ? c : best;
@@ -143,7 +150,7 @@ struct GroupMigration {
   uint64_t is;
 };
 
-template <bool TRACKED, bool RK = true>
+template <bool TRACKED, bool RK = true, int NN = 0>
 __device__ __forceinline__ void group_migration(const RunParams &p, uint32_t isl0, uint32_t G,
                                                 const uint32_t *__restrict__ tin,
                                                 const uint64_t *__restrict__ sin,
@@ -159,7 +166,7 @@ __device__ __forceinline__ void group_migration(const RunParams &p, uint32_t isl
   gm.it = 0;
   gm.is = 0;
   if (arrive) {
-    const uint32_t a = src * p.n + uindex(m.x, p.n);
+    const uint32_t a = src * (NN ? (uint32_t)NN : p.n) + uindex_nn<NN>(m.x, p.n);
     gm.it = __ldg(tin + a);
     if constexpr (TRACKED) gm.is = __ldg(sin + a);
   }
@@ -169,8 +176,8 @@ __device__ __forceinline__ void group_migration(const RunParams &p, uint32_t isl
   // (the multiply spreads bit d of `miss` to bit 8d without carries), then the
   // byte order reversed
   const uint32_t miss = ~bits & 0xFu;
-  const uint32_t fwd = uindex(m.x, p.n) | (uindex(m.y, p.n) << 8) | (uindex(m.z, p.n) << 16) |
-                       (uindex(m.w, p.n) << 24) |
+  const uint32_t fwd = uindex_nn<NN>(m.x, p.n) | (uindex_nn<NN>(m.y, p.n) << 8) |
+                       (uindex_nn<NN>(m.z, p.n) << 16) | (uindex_nn<NN>(m.w, p.n) << 24) |
                        (((miss * 0x00204081u) & 0x01010101u) * 0xFFu);
   gm.plan = (role == 4 && valid) ? __byte_perm(fwd, 0u, 0x0123u) : 0xFFFFFFFFu;
 }
@@ -267,7 +274,7 @@ __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &de
   for (uint32_t k = 0; k < kGroup; ++k)
     load_island<AP, TRACKED, NN>(p, isl0 + k, tin, sin, pt[k], ps[k]);
   GroupMigration gm;
-  if (do_mig) group_migration<TRACKED, RK>(p, isl0, G, tin, sin, gm);
+  if (do_mig) group_migration<TRACKED, RK, NN>(p, isl0, G, tin, sin, gm);
 #pragma unroll
   for (uint32_t k = 0; k < kGroup; k += ILV) {
     Words4 w[ILV][AP];
@@ -283,8 +290,8 @@ __device__ __forceinline__ void full_group(const RunParams &p, const Deposit &de
     uint64_t cs[ILV][AP];
 #pragma unroll
     for (int i = 0; i < ILV; ++i)
-      replicate<AP, TRACKED, T2, RK, TWO, DEL>(p, dep, isl0 + k + i, G, w[i], pt[k + i],
-                                               ps[k + i], ct[i], cs[i]);
+      replicate<AP, TRACKED, T2, RK, TWO, DEL, NN>(p, dep, isl0 + k + i, G, w[i], pt[k + i],
+                                                   ps[k + i], ct[i], cs[i]);
 #pragma unroll
     for (int i = 0; i < ILV; ++i)
       store_island<AP, TRACKED, NN>(p, isl0 + k + i, tout, sout, ct[i], cs[i]);
