@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(512)
   for (uint32_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n_items; i += nwarps) {
     const WorkItem w = items[i];
     const BatchRun &R = runs[w.run];
-    const RunParams p = R.p;
+    const RunParams &p = R.p;  // read in place (a copy would live in local memory)
     const uint32_t G = tick - R.start_tick;
     const uint32_t par = tick & 1u;
     const uint32_t *tin = R.trait[par];
