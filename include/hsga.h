@@ -58,7 +58,7 @@ typedef enum hsga_status {
   HSGA_ERR_CUDA = -3,         /* a CUDA runtime call failed */
   HSGA_ERR_DEVICE = -4,       /* a kernel reported an inconsistent state */
   HSGA_ERR_WAIT_TIMEOUT = -5, /* a bounded device-side wait ran out */
-  HSGA_ERR_UNSUPPORTED = -6   /* valid request this build cannot run */
+  HSGA_ERR_UNSUPPORTED = -6   /* valid request the library does not support */
 } hsga_status;
 
 /* Surface curation policies.  The paper defines steady (retained time points
