@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(1024)
   for (uint32_t size = 2; size <= K2; size <<= 1) {
     for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
       for (uint32_t i = threadIdx.x; i < K2 / 2; i += blockDim.x) {
-        const uint32_t lo = 2 * stride * (i / stride) + (i % stride);
+        // 2 stride floor(i / stride) + i mod stride, stride a power of two
+        const uint32_t lo = ((i & ~(stride - 1u)) << 1) | (i & (stride - 1u));
         const uint32_t hi = lo + stride;
         const bool up = ((lo & size) == 0);
         const unsigned long long a = pairs[lo], b = pairs[hi];
