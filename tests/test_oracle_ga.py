@@ -174,6 +174,30 @@ def test_degenerate_tori(orc, rows, cols):
         assert len(np.unique(t2)) >= c.agents - c.islands
 
 
+def test_later_direction_wins_a_shared_slot(orc):
+    """Step a2's order on a 1x2 torus with one agent per island: an island's
+    N and S neighbours are itself and its E and W neighbours the other
+    island, so its own emigrant and the other's can both land on its only
+    slot.  Directions land in the order N, E, S, W, a later arrival
+    overwrites an earlier one, and both emigrants are chosen before either
+    lands; the generations scanned include both orders of arrival."""
+    c = cfg(orc, rows=1, cols=2, n=1, seed=77)
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    trait = np.array([100, 200], np.uint32)
+    orders = set()
+    for G in range(400):
+        sent = [int(orc.philox4x32(key, (0xFFFFFFFF, i, G, 0))[1]) >> 30 for i in range(2)]
+        t2, _ = orc.migrate(c, trait, np.zeros(2, np.uint64), G)
+        for i in range(2):
+            src = [i, 1 - i, i, 1 - i]            # the N, E, S, W neighbours of island i
+            arrivals = [a for a in range(4) if sent[src[a]] == (a + 2) % 4]
+            want = trait[src[arrivals[-1]]] if arrivals else trait[i]
+            assert t2[i] == want, (G, i, sent)
+            if len(arrivals) == 2:
+                orders.add(tuple(src[a] == i for a in arrivals))
+    assert orders == {(True, False), (False, True)}
+
+
 def test_explicit_migrate_then_premigrated_run_equals_run(orc):
     c = cfg(orc, rows=5, cols=7, n=12, p_ben=0.01, policy=orc.TILTED, bits=2, seed=3)
     trait, surf = inputs.small_trait_population(c.agents, seed=8)
