@@ -61,6 +61,29 @@ def test_neutral_selection_is_wright_fisher(orc):
     assert abs(p_hat - 1 / c.n) < 6 * np.sqrt((1 / c.n) * (1 - 1 / c.n) / total) * 3
 
 
+def test_tournament_parent_is_the_fitter_candidate_first_on_ties(orc):
+    """Step a4 per child j of island i at generation G: candidates
+    floor(w0 n / 2^32) and floor(w1 n / 2^32) of Philox(seed; j, i, G, 1); the
+    parent is the second only if it is strictly fitter.  Few trait levels make
+    ties between distinct candidates common, which the marginal parent law
+    cannot show (it is the same whichever candidate keeps ties)."""
+    c = cfg(orc, rows=4, cols=4, n=16, tournament=2, interval=0, seed=19)
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    trait, surf = inputs.small_trait_population(c.agents, seed=4)
+    G = 9
+    _, _, par = orc.run(c, trait, surf, G0=G, generations=1, track_parents=True)
+    ties = 0
+    for a in range(c.agents):
+        i, j = divmod(a, c.n)
+        w = orc.philox4x32(key, (j, i, G, 1))
+        ca, cb = (int(w[0]) * c.n) >> 32, (int(w[1]) * c.n) >> 32
+        fa, fb = trait[i * c.n + ca], trait[i * c.n + cb]
+        want = cb if fb > fa else ca
+        assert int(par[0][a]) == i * c.n + want, a
+        ties += int(ca != cb and fa == fb)
+    assert ties > c.agents // 10
+
+
 def test_neutral_traits_stay_zero(orc):
     c = cfg(orc, rows=4, cols=4, n=32)
     trait, _, _ = orc.run(c, generations=500)
