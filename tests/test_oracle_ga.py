@@ -159,6 +159,12 @@ def test_migration_copies_from_von_neumann_neighbours(orc):
     nb = np.array([[orc.neighbour(c, i, d) for d in range(4)] for i in range(c.islands)])
     # every immigrant comes from one of the four neighbours
     assert np.all((nb[isl[foreign]] == home[foreign][:, None]).any(axis=1))
+    # ... the one whose emigrant was aimed at this island: direction w1 >> 30
+    # of Philox(seed; 0xFFFFFFFF, source, G, 0) points from the source here
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    aim = np.array([int(orc.philox4x32(key, (0xFFFFFFFF, i, 17, 0))[1]) >> 30
+                    for i in range(c.islands)])
+    assert np.all(nb[home[foreign], aim[home[foreign]]] == isl[foreign])
     # an emigrant lands at most once (a copy is sent, not broadcast)
     vals, cnt = np.unique(t2[foreign], return_counts=True)
     assert cnt.max() == 1
