@@ -162,9 +162,13 @@ def test_migration_copies_from_von_neumann_neighbours(orc):
     # ... the one whose emigrant was aimed at this island: direction w1 >> 30
     # of Philox(seed; 0xFFFFFFFF, source, G, 0) points from the source here
     key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
-    aim = np.array([int(orc.philox4x32(key, (0xFFFFFFFF, i, 17, 0))[1]) >> 30
-                    for i in range(c.islands)])
+    blocks = np.array([orc.philox4x32(key, (0xFFFFFFFF, i, 17, 0)) for i in range(c.islands)],
+                      dtype=np.uint64)
+    aim = (blocks[:, 1] >> np.uint64(30)).astype(np.int64)
     assert np.all(nb[home[foreign], aim[home[foreign]]] == isl[foreign])
+    # ... and it is that source's member at slot floor(w0 n / 2^32)
+    eslot = ((blocks[:, 0] * np.uint64(c.n)) >> np.uint64(32)).astype(np.int64)
+    assert np.all(t2[foreign] % c.n == eslot[home[foreign]])
     # an emigrant lands at most once (a copy is sent, not broadcast)
     vals, cnt = np.unique(t2[foreign], return_counts=True)
     assert cnt.max() == 1
