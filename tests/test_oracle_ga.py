@@ -169,6 +169,14 @@ def test_migration_copies_from_von_neumann_neighbours(orc):
     # ... and it is that source's member at slot floor(w0 n / 2^32)
     eslot = ((blocks[:, 0] * np.uint64(c.n)) >> np.uint64(32)).astype(np.int64)
     assert np.all(t2[foreign] % c.n == eslot[home[foreign]])
+    # ... landing, from direction d, at slot floor(v_d n / 2^32) of the
+    # receiver's Philox(seed; 0xFFFFFFFE, island, G, 0)
+    place = np.array([orc.philox4x32(key, (0xFFFFFFFE, i, 17, 0)) for i in range(c.islands)],
+                     dtype=np.uint64)
+    recv = isl[foreign]
+    d_in = (nb[recv] == home[foreign][:, None]).argmax(axis=1)
+    pslot = ((place[recv, d_in] * np.uint64(c.n)) >> np.uint64(32)).astype(np.int64)
+    assert np.all(np.nonzero(foreign)[0] % c.n == pslot)
     # an emigrant lands at most once (a copy is sent, not broadcast)
     vals, cnt = np.unique(t2[foreign], return_counts=True)
     assert cnt.max() == 1
