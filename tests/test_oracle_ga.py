@@ -61,13 +61,16 @@ def test_neutral_selection_is_wright_fisher(orc):
     assert abs(p_hat - 1 / c.n) < 6 * np.sqrt((1 / c.n) * (1 - 1 / c.n) / total) * 3
 
 
-def test_tournament_parent_is_the_fitter_candidate_first_on_ties(orc):
-    """Step a4 per child j of island i at generation G: candidates
-    floor(w0 n / 2^32) and floor(w1 n / 2^32) of Philox(seed; j, i, G, 1); the
-    parent is the second only if it is strictly fitter.  Few trait levels make
-    ties between distinct candidates common, which the marginal parent law
-    cannot show (it is the same whichever candidate keeps ties)."""
-    c = cfg(orc, rows=4, cols=4, n=16, tournament=2, interval=0, seed=19)
+@pytest.mark.parametrize("t", [2, 5, 7])
+def test_tournament_parent_is_the_fitter_candidate_first_on_ties(orc, t):
+    """Step a4 per child j of island i at generation G: candidate 0 and 1 are
+    floor(w n / 2^32) of words 0 and 1 of Philox(seed; j, i, G, 1), candidate
+    c >= 2 of word (c - 2) mod 4 of Philox(seed; j, i, G, 2 + (c - 2) // 4);
+    a later candidate replaces the best only if strictly fitter.  Few trait
+    levels make ties between distinct candidates common, which the marginal
+    parent law cannot show (it is the same whichever candidate keeps ties),
+    and words reused across blocks would keep that law too."""
+    c = cfg(orc, rows=4, cols=4, n=16, tournament=t, interval=0, seed=19 + t)
     key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
     trait, surf = inputs.small_trait_population(c.agents, seed=4)
     G = 9
@@ -76,11 +79,17 @@ def test_tournament_parent_is_the_fitter_candidate_first_on_ties(orc):
     for a in range(c.agents):
         i, j = divmod(a, c.n)
         w = orc.philox4x32(key, (j, i, G, 1))
-        ca, cb = (int(w[0]) * c.n) >> 32, (int(w[1]) * c.n) >> 32
-        fa, fb = trait[i * c.n + ca], trait[i * c.n + cb]
-        want = cb if fb > fa else ca
-        assert int(par[0][a]) == i * c.n + want, a
-        ties += int(ca != cb and fa == fb)
+        words = [int(w[0]), int(w[1])]
+        for b in range((t - 2 + 3) // 4):
+            words += [int(x) for x in orc.philox4x32(key, (j, i, G, 2 + b))]
+        cands = [(x * c.n) >> 32 for x in words[:t]]
+        best = cands[0]
+        for cand in cands[1:]:
+            fb, fc = trait[i * c.n + best], trait[i * c.n + cand]
+            ties += int(cand != best and fc == fb)
+            if fc > fb:
+                best = cand
+        assert int(par[0][a]) == i * c.n + best, a
     assert ties > c.agents // 10
 
 
