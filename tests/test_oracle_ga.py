@@ -148,6 +148,35 @@ def test_deposit_touches_only_the_site(orc, policy, bits):
             assert stats.chisquare(counts).pvalue > 1e-4
 
 
+def test_child_takes_word_2_for_mutation_and_word_3_for_deposit(orc):
+    """Per child j of island i at generation G, with (w0..w3) =
+    Philox(seed; j, i, G, 1): the trait is the parent's, raised by one when
+    w2 < floor(p_ben 2^32), else lowered by one when w2 < floor(p_ben 2^32) +
+    floor(p_del 2^32) (saturating), and the surface is the parent's with the
+    generation's site set to the low b bits of w3.  Rates and uniformity
+    alone would not show which word feeds which step."""
+    c = cfg(orc, rows=4, cols=4, n=16, policy=orc.TILTED, bits=2, interval=0,
+            p_ben=0.3, p_del=0.3, seed=23)
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    trait, surf = inputs.small_trait_population(c.agents, seed=6)
+    G = 21
+    t2, s2, par = orc.run(c, trait, surf, G0=G, generations=1, track_parents=True)
+    tb, td = int(0.3 * 2**32), int(0.3 * 2**32)
+    site = orc.site(orc.TILTED, 32, c.W, G)
+    mask = 3 << (2 * site)
+    for a in range(c.agents):
+        i, j = divmod(a, c.n)
+        w = orc.philox4x32(key, (j, i, G, 1))
+        p = int(par[0][a])
+        want_t = int(trait[p])
+        if int(w[2]) < tb:
+            want_t = min(want_t + 1, 2**32 - 1)
+        elif int(w[2]) < tb + td:
+            want_t = max(want_t - 1, 0)
+        want_s = (int(surf[p]) & ~mask) | ((int(w[3]) & 3) << (2 * site))
+        assert int(t2[a]) == want_t and int(s2[a]) == want_s, a
+
+
 def test_untracked_leaves_surface_alone(orc):
     c = cfg(orc, policy=orc.NONE, p_ben=0.05)
     trait, surf = inputs.random_population(c.agents, seed=3, trait_max=10)
