@@ -312,6 +312,30 @@ def test_cone_equals_full_grid(orc):
 
 # ---------------------------------------------------------------- a7 ---
 
+def test_sample_follows_its_draws(orc):
+    """Step a7 per sample: the j-th pick swaps position j with position
+    j + floor(w0 (I - j) / 2^32) of the island list, w0 word 0 of
+    Philox(seed; j, 0xFFFFFFFF, G, 3), and the genome taken from island i is
+    its member at floor(w0 n / 2^32) of Philox(seed; 0xFFFFFFFD, i, G, 0)."""
+    c = cfg(orc, rows=6, cols=7, n=12, seed=29)
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    trait = np.arange(c.agents, dtype=np.uint32)
+    surf = np.zeros(c.agents, dtype=np.uint64)
+    I = c.islands
+    for G, k in ((0, 1), (5, 17), (77, I)):
+        w, where = orc.sample(c, trait, surf, G, k)
+        perm = list(range(I))
+        for j in range(k):
+            d = int(orc.philox4x32(key, (j, 0xFFFFFFFF, G, 3))[0])
+            r = j + ((d * (I - j)) >> 32)
+            perm[j], perm[r] = perm[r], perm[j]
+        for j in range(k):
+            isl = perm[j]
+            slot = (int(orc.philox4x32(key, (0xFFFFFFFD, isl, G, 0))[0]) * c.n) >> 32
+            assert (int(where[j, 0]), int(where[j, 1])) == (isl, slot), (G, j)
+            assert int(w[j, 0]) == isl * c.n + slot
+
+
 def test_sample_distinct_and_uniform(orc):
     c = cfg(orc, rows=2, cols=2, n=5, seed=13)
     trait = np.arange(c.agents, dtype=np.uint32)
