@@ -20,25 +20,39 @@ def test_hybrid_halves_are_steady_and_tilted(orc, S, W):
         assert list(got[S // 2:]) == list(orc.lookup(orc.TILTED, S // 2, W, T))
 
 
-def test_hybrid_deposits_two_independent_differentiae(orc):
+@pytest.mark.parametrize("T", [77, 79])
+def test_hybrid_deposits_two_independent_differentiae(orc, T):
+    """Hybrid deposition T writes the steady half (sites [0, S/2); it may
+    discard, as at T = 77) and the tilted half (sites [S/2, S)): the steady
+    field from the low b bits of word 3 of the child's replication block, the
+    tilted one from the b bits at bit 16 of it.  Nothing else changes, and the
+    two values are independent and uniform."""
     c = orc.Config(rows=16, cols=16, n=32, policy=HYBRID, bits=2, interval=0, seed=3)
     trait, surf = inputs.small_trait_population(c.agents, seed=2)
-    S, T = 32, 77
+    S, half = 32, 16
     _, child, par = orc.run(c, trait, surf, G0=T, generations=1, track_parents=True)
     parent = surf[par[0].astype(np.int64)]
-    sa = orc.site(orc.STEADY, S // 2, 2, T)
-    sb = S // 2 + orc.site(orc.TILTED, S // 2, 2, T)
-    mask = np.uint64(0)
-    for s_ in (sa, sb):
-        if s_ < S:
-            mask |= np.uint64(3 << (2 * s_))
+    sa = orc.site(orc.STEADY, half, 2, T)               # == half: discarded
+    sb = half + orc.site(orc.TILTED, half, 2, T)
+    assert (sa == half) == (T == 77)
+    mask = np.uint64(3 << (2 * sb))
+    if sa < half:
+        mask |= np.uint64(3 << (2 * sa))
     assert np.all(((child ^ parent) & ~mask) == 0)
-    va = ((child >> np.uint64(2 * sa)) & np.uint64(3)).astype(np.int64)
     vb = ((child >> np.uint64(2 * sb)) & np.uint64(3)).astype(np.int64)
-    table = np.zeros((4, 4))
-    np.add.at(table, (va, vb), 1)
-    assert stats.chi2_contingency(table).pvalue > 1e-4           # independent
-    assert stats.chisquare(table.sum(axis=1)).pvalue > 1e-4      # uniform
+    assert stats.chisquare(np.bincount(vb, minlength=4)).pvalue > 1e-4      # uniform
+    if sa < half:
+        va = ((child >> np.uint64(2 * sa)) & np.uint64(3)).astype(np.int64)
+        table = np.zeros((4, 4))
+        np.add.at(table, (va, vb), 1)
+        assert stats.chi2_contingency(table).pvalue > 1e-4                  # independent
+    key = (c.seed & 0xFFFFFFFF, c.seed >> 32)
+    for a in range(0, c.agents, 7):
+        i, j = divmod(a, c.n)
+        w3 = int(orc.philox4x32(key, (j, i, T, 1))[3])
+        assert int(vb[a]) == (w3 >> 16) & 3, a
+        if sa < half:
+            assert int(va[a]) == w3 & 3, a
 
 
 @pytest.mark.parametrize("k", [2, 3, 8])
