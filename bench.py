@@ -4,10 +4,10 @@ x 32 agents = 16,777,216 agents, 3 x uint32 genomes (trait + 64-bit tilted
 surface of 1-bit differentiae), tournament 2, beneficial mutation 1e-3,
 synchronous migration every generation (the bit-exact mode).
 
-One step = GENS_PER_STEP generations of steps a1-a6 over the whole grid plus
-step a7 (10,000 sampled genomes).  Inputs live in HBM: the population is
-201 MB per plane, larger than the 129 MB L2, so no flush is needed between
-launches.
+One step = GENS_PER_STEP (1,000) generations of steps a1-a6 over the whole
+grid plus step a7 (10,000 sampled genomes).  Inputs live in HBM: the
+population is 201 MB per plane, larger than the 129 MB L2, so no flush is
+needed between launches.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ROWS, COLS, N_AGENTS = 512, 1024, 32
-GENS_PER_STEP = 200
+GENS_PER_STEP = 1000
 SAMPLE_K = 10000
 WORKLOAD = dict(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy="tilted", bits=1, W=2,
                 interval=1, p_ben=1e-3, p_del=0.0)
@@ -43,16 +43,15 @@ AGENTS = ROWS * COLS * N_AGENTS
 BYTES_PER_LAUNCH = AGENTS * 24 + ROWS * COLS * 12
 
 
-def config_json(extra=None):
-    c = {"workload": "wafer-shaped island GA, sync migration (512x1024 islands x 32 agents)",
-         "islands": ROWS * COLS, "agents": AGENTS, "agents_per_island": N_AGENTS,
-         "genome": "3 x uint32 (trait + 64-bit tilted surface, 1-bit differentiae)",
-         "tournament": 2, "p_beneficial": 1e-3, "generations_per_step": GENS_PER_STEP,
-         "sample_per_step": SAMPLE_K, "kernel": "streamed",
-         "l2": "inputs larger than L2 (201 MB per population plane)"}
-    if extra:
-        c.update(extra)
-    return c
+def config_json(world: int = 1):
+    """The workload, the same on both arms (each arm's step is described
+    beside it, under "step")."""
+    return {"workload": "wafer-shaped island GA, sync migration (512x1024 islands x 32 agents)",
+            "islands": ROWS * COLS, "agents": AGENTS, "agents_per_island": N_AGENTS,
+            "genome": "3 x uint32 (trait + 64-bit tilted surface, 1-bit differentiae)",
+            "tournament": 2, "p_beneficial": 1e-3, "migration": "synchronous, every generation",
+            "l2": "inputs larger than L2 (201 MB per population plane)",
+            "parallelism": f"replicas{world}"}
 
 
 def measured_peaks():
@@ -115,7 +114,7 @@ class ClockSampler:
             self.out = open(f"/tmp/hsga_clocks_{os.getpid()}.csv", "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -185,55 +184,158 @@ def barrier(world: int):
         dist.barrier()
 
 
-def cpu_baseline_oracle(generations: int = 25):
-    """The oracle as it stands, single-threaded, on this host: the same
-    workload's first `generations` generations from founders."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_config(seed: int):
+    import oracle
+    return oracle.Config(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy=oracle.TILTED,
+                         bits=1, W=2, interval=1, p_ben=1e-3, seed=seed)
+
+
+def _oracle_replica_run(job):
+    """One host core's replica: the workload's first `generations`
+    generations from founders with its own seed.  Returns wall-clock start
+    and end (comparable across processes)."""
+    seed, generations = job
     import oracle
     oracle.build()
-    cfg = oracle.Config(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy=oracle.TILTED,
-                        bits=1, W=2, interval=1, p_ben=1e-3, seed=1)
-    t0 = time.perf_counter()
+    cfg = oracle_config(seed)
+    t0 = time.time()
     oracle.run(cfg, generations=generations)
-    dt = time.perf_counter() - t0
-    return {"value": AGENTS * generations / dt, "unit": "agent replications/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{generations} generations of the full 16.8M-agent grid from founders "
-                      f"({AGENTS * generations:.3g} replications, {dt:.1f} s, single thread)"}
+    return t0, time.time()
+
+
+def cpu_baseline_oracle(generations: int = 12):
+    """The oracle as it stands (plain single-threaded C) on every host core
+    at once: one independent replica of the workload per core (own seed),
+    each running its first `generations` generations from founders.  The
+    pool is spawned, never forked, because CUDA is initialised already."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    jobs = [(1 + i, generations) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        spans = pool.map(_oracle_replica_run, jobs, chunksize=1)
+    per_core = [AGENTS * generations / (b - a) for a, b in spans]
+    wall = max(b for _, b in spans) - min(a for a, _ in spans)
+    total = AGENTS * generations * cores
+    return {"value": total / wall, "unit": "agent replications/s", "cores": cores,
+            "kind": "oracle", "per_core": statistics.median(per_core),
+            "sample": f"one replica per host core ({cores} processes, seeds 1..{cores}), each "
+                      f"{generations} generations of the full 16.8M-agent grid from founders "
+                      f"({total:.3g} replications in {wall:.1f} s wall; median "
+                      f"{statistics.median(per_core):.3g} replications/s per core)"}
+
+
+def _oracle_replica_server(conn, seed):
+    """Reference-arm worker: holds one replica of the workload and advances
+    it one generation per request, replying with the seconds it took."""
+    import oracle
+    oracle.build()
+    cfg = oracle_config(seed)
+    trait, surf = oracle.founders(cfg)
+    G = 0
+    while True:
+        if conn.recv() is None:
+            break
+        t0 = time.perf_counter()
+        trait, surf, _ = oracle.run(cfg, trait, surf, G0=G, generations=1)
+        G += 1
+        conn.send(time.perf_counter() - t0)
+    conn.close()
 
 
 def run_reference(args):
+    """The oracle as the reference arm: one replica of the workload per host
+    core (spawned processes, own seeds); a step advances every replica by one
+    generation of the full grid (a bounded sample of the workload)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import multiprocessing as mp
     import oracle
     oracle.build()
-    cfg = oracle.Config(rows=ROWS, cols=COLS, n=N_AGENTS, tournament=2, policy=oracle.TILTED,
-                        bits=1, W=2, interval=1, p_ben=1e-3, seed=1)
-    trait, surf = oracle.founders(cfg)
-    G = 0
-    # one step = one generation of the full grid (bounded CPU sample)
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    pipes, procs = [], []
+    for i in range(cores):
+        a, b = ctx.Pipe()
+        pr = ctx.Process(target=_oracle_replica_server, args=(b, 1 + i), daemon=True)
+        pr.start()
+        pipes.append(a)
+        procs.append(pr)
+
+    def step():
+        for c in pipes:
+            c.send(1)
+        for c in pipes:
+            c.recv()
+
     for _ in range(args.warmup):
-        trait, surf, _ = oracle.run(cfg, trait, surf, G0=G, generations=1)
-        G += 1
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        trait, surf, _ = oracle.run(cfg, trait, surf, G0=G, generations=1)
-        G += 1
+        step()
     dt = time.perf_counter() - t0
-    value = AGENTS * args.steps / dt
+    for c in pipes:
+        c.send(None)
+    for pr in procs:
+        pr.join(timeout=30)
+    value = AGENTS * cores * args.steps / dt
+    sample = (f"{args.steps} timed steps; a step = one generation of the full grid on each of "
+              f"{cores} replicas (one per host core, seeds 1..{cores})")
     line = {"impl": "reference", "metric": "agent replications/sec", "value": value,
             "unit": "agent replications/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
-            "config": config_json({"generations_per_step": 1, "sample_per_step": 0,
-                                   "kernel": "CPU oracle (plain C, single thread)"}),
-            "cpu_baseline": {"value": value, "unit": "agent replications/s", "cores": 1,
-                             "kind": "oracle",
-                             "sample": f"{args.steps} timed generations of the full grid"},
+            "data": "synthetic", "config": config_json(),
+            "step": {"generations": 1, "replicas": cores, "sample_genomes": 0,
+                     "engine": "CPU oracle (plain C, one single-threaded process per core)"},
+            "cpu_baseline": {"value": value, "unit": "agent replications/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "agent replications/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def philox_peak(stream) -> dict:
+    """Measured ceiling of the integer-issue bound: Philox4x32-10 blocks per
+    second drawn by hsga_philox_throughput (the generation kernels' form of
+    the generator) over every SM at full occupancy, timed with CUDA events on
+    its stream.  Every replication draws one block, so replications/s can
+    not exceed this."""
+    import torch
+    from paper_2404_10861_gb300 import binding as hb
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    threads, m = sms * 2048, 2048
+    out = torch.empty(threads, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        hb.hsga_philox_throughput(7, threads, m, 0, 1, out, stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        hb.hsga_philox_throughput(7, threads, m, 0, 1, out, stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    return {"blocks_per_s": threads * m * reps / sec, "kernel": "philox_throughput_kernel",
+            "launch": f"{threads} threads x {m} blocks, {reps} launches",
+            "ms_per_launch": sec * 1e3 / reps}
+
+
+def alu_roofline(reps_per_s: float, peak: dict) -> dict:
+    return {"bound": "alu", "achieved": reps_per_s, "peak": peak["blocks_per_s"],
+            "unit": "replications/s (one Philox4x32-10 block each)",
+            "frac": reps_per_s / peak["blocks_per_s"],
+            "peak_kind": "measured in this run: Philox blocks/s of hsga_philox_throughput",
+            "peak_ms_per_launch": peak["ms_per_launch"]}
 
 
 def run_ours(args):
@@ -287,6 +389,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the streamed generation kernel)
     per_launch_s = gen_ms / 1e3 / (GENS_PER_STEP * args.steps)
+    alu_peak = philox_peak(stream)
     achieved = BYTES_PER_LAUNCH / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic()
@@ -337,7 +440,9 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "u32", "data": "synthetic",
-                "config": config_json({"parallelism": f"replicas{world}"}),
+                "config": config_json(world),
+                "step": {"generations": GENS_PER_STEP, "sample_genomes": SAMPLE_K,
+                         "kernel": "step_streamed_kernel (one generation per launch)"},
                 "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
@@ -345,6 +450,7 @@ def run_ours(args):
                              "kernel": "step_streamed_kernel", "peak_kind": peak_kind,
                              "algorithmic_bytes_per_launch": BYTES_PER_LAUNCH,
                              "avg_launch_us": per_launch_s * 1e6},
+                "alu": alu_roofline(value / world, alu_peak),
                 "sample_ms_per_step": sample_ms / args.steps,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
@@ -393,19 +499,15 @@ def run_secondary(args):
                     "value": agents * gens * args.steps / (ms / 1e3),
                     "ms_per_step": ms / args.steps, "us_per_generation": ms * 1e3 / (gens * args.steps),
                     "islands_per_warp": st["islands_per_warp"], "blocks": st["blocks"]})
-    # the resident path's roofline is integer issue: 100 operations per
-    # replication against 152 SMs x 4 schedulers x 32 lanes at 2,070 MHz
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    alu_peak = sms * 4 * 32 * 2070e6 / 1e12
+    # the resident path's roofline is integer issue: every replication draws
+    # one Philox block, against the measured block rate of the generator
     best = max(out, key=lambda r: r["value"])
-    alu = best["value"] * 100 / 1e12
+    alu = dict(alu_roofline(best["value"], philox_peak(torch.cuda.Stream())),
+               kernel=best["kernel"])
     print(json.dumps({"metric": "agent replications/sec", "unit": "agent replications/s",
                       "workload": args.workload, "config": dict(kw, generations_per_step=gens),
                       "steps": args.steps, "warmup": args.warmup, "dtype": "u32",
-                      "data": "synthetic", "kernels": out,
-                      "alu": {"kernel": best["kernel"], "achieved": alu, "peak": alu_peak,
-                              "unit": "Tops/s", "frac": alu / alu_peak,
-                              "ops_per_replication": 100}}), flush=True)
+                      "data": "synthetic", "kernels": out, "alu": alu}), flush=True)
 
 
 def splitmix64(x: int) -> int:
@@ -546,18 +648,19 @@ def run_async_wafer(args, mode="async"):
         out.append({"generations_per_launch": K, "generations": gens,
                     "value": AGENTS * gens / (ms / 1e3), "us_per_generation": ms * 1e3 / gens})
     # Every genome streams through HBM each generation (the grid is far larger
-    # than what stays on chip): algorithmic bytes per agent-generation are the
-    # 16-byte genome (trait, surface, counter) read and written plus the
-    # exchange state per island spread over its agents (see the design notes);
-    # the ALU view counts 100 integer operations per replication (80 for the
-    # Philox4x32-10 block, the rest tournament, mutation and deposit).
+    # than what stays on chip).  Algorithmic bytes per agent-generation: the
+    # 16-byte genome (trait, 64-bit surface, counter) read and written = 32 B,
+    # plus the exchange state of its island spread over the island's 32
+    # agents.  Latest-emigrant records: a 32-byte record written and read and
+    # 16 B of seen-stamps read and written per island = 96 B / 32 = 3 B, for
+    # 35 B.  Per-neighbour buffers: the island's lane state, channel words
+    # and acknowledgements add 13 B per agent, for 45 B.  The ALU view: every replication draws one Philox block, against the
+    # measured block rate of the generator.
     best = max(out, key=lambda r: r["value"])
     bytes_per_agent = {"async": 35.0, "buffered": 45.0}[mode]
     peak, peak_kind = measured_peaks()
     gbs = best["value"] * bytes_per_agent / 1e9
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    alu_peak = sms * 4 * 32 * 2070e6 / 1e12             # thread-ops/s, at the 2070 MHz maximum
-    alu = best["value"] * 100 / 1e12
+    alu = alu_roofline(best["value"], philox_peak(stream))
     label = {"async": "free-running migration, latest-emigrant records",
              "buffered": "free-running migration, per-neighbour buffers"}[mode]
     # DRAM traffic from the committed ncu capture (bytes per generation; a
@@ -574,8 +677,7 @@ def run_async_wafer(args, mode="async"):
                                    "traffic_per_generation": per_gen, "peak_kind": peak_kind,
                                    "generations_per_launch": best["generations_per_launch"],
                                    "algorithmic_bytes_per_agent_generation": bytes_per_agent},
-                      "alu": {"achieved": alu, "peak": alu_peak, "unit": "Tops/s",
-                              "frac": alu / alu_peak, "ops_per_replication": 100},
+                      "alu": alu,
                       "dtype": "u32",
                       "data": "synthetic"}), flush=True)
 

@@ -351,6 +351,17 @@ int hsga_wait_probe(const uint64_t *record_dev, uint32_t seq, uint64_t limit_ns,
 int hsga_philox_device(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1, uint32_t c2,
                        uint32_t c3, uint32_t *out_dev, void *cuda_stream);
 
+/* Throughput of the same generator in the form the generation kernels
+ * evaluate it (round keys held in the kernel's parameter block), for the
+ * path's integer-issue ceiling: every replication (steps a4-a6) draws one
+ * block, so no kernel of the path can replicate faster than this kernel
+ * draws blocks.  Thread t < threads evaluates the blocks for counters
+ * (i, t, c2, c3), i < blocks_per_thread, and stores the xor of all their
+ * words in out_dev[t] (device uint32; threads <= 2^30, else
+ * HSGA_ERR_INVALID_ARG).  Stream-ordered on cuda_stream. */
+int hsga_philox_throughput(uint64_t seed, uint32_t threads, uint32_t blocks_per_thread,
+                           uint32_t c2, uint32_t c3, uint32_t *out_dev, void *cuda_stream);
+
 /* Phylogeny reconstruction on the GPU from k sampled surfaces (of
  * surface_words 64-bit words each, agent-major; 0 means 1) that all
  * elapsed `generations` generations (synchronous mode, or free-running
@@ -454,17 +465,21 @@ void hsga_batch_destroy(hsga_batch *b);
  * paper has no counterpart; it is an interface convenience of this library.
  *   cfg: run configuration (cfg->kernel is ignored); rows*cols <= 8192
  *        islands, else HSGA_ERR_INVALID_ARG.
- *   generation: G of the population on entry (the result is at G + n).
- *   trait, surf: device planes, layout as hsga_set_population; surf may be
- *        NULL only for HSGA_NONE.  Host pointers are HSGA_ERR_INVALID_ARG.
+ *   generation: G of the population on entry (the result is at G + n);
+ *        G + n must stay below 2^32 - 64, else HSGA_ERR_INVALID_ARG.
+ *   trait, surf: device planes on the current device, layout as
+ *        hsga_set_population; surf may be NULL only for HSGA_NONE.  Host
+ *        pointers and planes on another device are HSGA_ERR_INVALID_ARG.
  * Scratch (stamped migrant records and an error word: ~512 KiB) is one
  * array built into the library and held on every device that loads it until
  * exit.  The first call on a device looks its address up
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * All calls share the array: calls whose work overlaps on the GPU race.  The
- * call is stream-ordered on cuda_stream and waits for it before returning the
- * kernels' status (HSGA_ERR_WAIT_TIMEOUT / HSGA_ERR_DEVICE on a device-side
- * error). */
+ * (cudaGetSymbolAddress), so make that first call before any stream capture;
+ * the address is kept until exit, so calls after a device reset are not
+ * supported.  All calls share the array: calls whose work overlaps on the
+ * GPU race.  The work is stream-ordered on cuda_stream; the call then waits
+ * for that stream and reads the kernels' error word back to the host before
+ * it returns their status (HSGA_ERR_WAIT_TIMEOUT / HSGA_ERR_DEVICE on a
+ * device-side error). */
 int hsga_run_generations_noalloc(const hsga_config *cfg, uint64_t generation,
                                  uint64_t n_generations, uint32_t *trait,
                                  uint64_t *surf, void *cuda_stream);

@@ -130,6 +130,9 @@ _SIGS = {
                            ctypes.c_int),
     "hsga_batch_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_batch_destroy": ([ctypes.c_void_p], None),
+    "hsga_philox_throughput": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                ctypes.c_void_p], ctypes.c_int),
     "hsga_run_generations_noalloc": ([ctypes.POINTER(hsga_config), ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p], ctypes.c_int),
@@ -330,6 +333,15 @@ def hsga_philox_device(seed: int, c0: int, count: int, c1: int, c2: int, c3: int
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(lib().hsga_philox_device(seed, c0, count, c1, c2, c3, _ptr(out_dev), s),
            "hsga_philox_device")
+
+
+def hsga_philox_throughput(seed: int, threads: int, blocks_per_thread: int, c2: int, c3: int,
+                           out_dev, stream=None):
+    """Per thread t, the xor of every word of the blocks for counters
+    (i, t, c2, c3), i < blocks_per_thread, into a device uint32 buffer."""
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().hsga_philox_throughput(seed, threads, blocks_per_thread, c2, c3,
+                                        _ptr(out_dev), s), "hsga_philox_throughput")
 
 
 def hsga_synchronize(g):

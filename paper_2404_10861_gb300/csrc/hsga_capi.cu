@@ -937,6 +937,14 @@ int hsga_philox_device(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1, 
       launch_philox_sweep(seed, c0, count, c1, c2, c3, out_dev, (cudaStream_t)cuda_stream));
 }
 
+int hsga_philox_throughput(uint64_t seed, uint32_t threads, uint32_t blocks_per_thread,
+                           uint32_t c2, uint32_t c3, uint32_t *out_dev, void *cuda_stream) {
+  if (threads > 0 && !out_dev) return HSGA_ERR_INVALID_ARG;
+  if (threads > (1u << 30)) return HSGA_ERR_INVALID_ARG;
+  return cuda_status(launch_philox_throughput(seed, threads, blocks_per_thread, c2, c3, out_dev,
+                                              (cudaStream_t)cuda_stream));
+}
+
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
                       uint32_t *out_dev, void *cuda_stream) {
   if (count > 0 && !out_dev) return HSGA_ERR_INVALID_ARG;

@@ -96,6 +96,8 @@ cudaError_t launch_wait_probe(const uint64_t *record, uint32_t seq, uint64_t lim
                               uint64_t *out, cudaStream_t stream);
 cudaError_t launch_philox_sweep(uint64_t seed, uint32_t c0, uint32_t count, uint32_t c1,
                                 uint32_t c2, uint32_t c3, uint32_t *out, cudaStream_t stream);
+cudaError_t launch_philox_throughput(uint64_t seed, uint32_t threads, uint32_t m, uint32_t c2,
+                                     uint32_t c3, uint32_t *out, cudaStream_t stream);
 cudaError_t launch_sites(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0, uint64_t count,
                          uint32_t *out, cudaStream_t stream);
 

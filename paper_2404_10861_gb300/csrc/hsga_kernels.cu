@@ -329,6 +329,45 @@ cudaError_t launch_philox_sweep(uint64_t seed, uint32_t c0, uint32_t count, uint
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------- Philox throughput ---
+// Thread t draws the blocks for counters (i, t, c2, c3), i < m, in the form
+// the generation kernels use (round keys in the parameter block), four
+// independent chains at a time, and stores the xor of every word it drew
+// (so that no draw can be optimised away).
+__global__ void __launch_bounds__(256)
+    philox_throughput_kernel(RunParams p, uint32_t threads, uint32_t m, uint32_t c2,
+                             uint32_t c3, uint32_t *__restrict__ out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= threads) return;
+  uint32_t acc = 0;
+  uint32_t i = 0;
+  for (; i + 4 <= m; i += 4) {
+    const Words4 a = philox_rk(p, i, t, c2, c3);
+    const Words4 b = philox_rk(p, i + 1, t, c2, c3);
+    const Words4 c = philox_rk(p, i + 2, t, c2, c3);
+    const Words4 d = philox_rk(p, i + 3, t, c2, c3);
+    acc ^= (a.x ^ a.y ^ a.z ^ a.w) ^ (b.x ^ b.y ^ b.z ^ b.w) ^ (c.x ^ c.y ^ c.z ^ c.w) ^
+           (d.x ^ d.y ^ d.z ^ d.w);
+  }
+  for (; i < m; ++i) {
+    const Words4 a = philox_rk(p, i, t, c2, c3);
+    acc ^= a.x ^ a.y ^ a.z ^ a.w;
+  }
+  out[t] = acc;
+}
+
+cudaError_t launch_philox_throughput(uint64_t seed, uint32_t threads, uint32_t m, uint32_t c2,
+                                     uint32_t c3, uint32_t *out, cudaStream_t stream) {
+  if (threads == 0) return cudaSuccess;
+  RunParams p{};
+  p.k0 = (uint32_t)seed;
+  p.k1 = (uint32_t)(seed >> 32);
+  set_round_keys(p);
+  const uint32_t blocks = (threads + 255) / 256;
+  philox_throughput_kernel<<<blocks, 256, 0, stream>>>(p, threads, m, c2, c3, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------- site function ---
 __global__ void sites_kernel(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                              uint64_t count, uint32_t *out) {

@@ -15,9 +15,12 @@
 // address, so the address is looked up once per device with
 // cudaGetSymbolAddress (on the first call on that device, with that device
 // current) and passed to the kernel.  That first call should therefore come
-// before any stream capture.  All calls share the one array and it keeps the
-// last call's contents: each call clears the records and the error word it
-// relies on, and calls whose work overlaps on the GPU race on it.
+// before any stream capture.  The address is kept for the life of the
+// process, so calling the entry point after a device reset is not supported.
+// All calls share the one array and it keeps the last call's contents: each
+// call clears the records and the error word it relies on, and calls whose
+// work overlaps on the GPU race on it.  Every call waits for its stream and
+// reads the kernels' error word back before it returns.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -57,13 +60,16 @@ int scratch_address(unsigned char **out) {
   return HSGA_OK;
 }
 
-bool on_device(const void *ptr) {
+// Device memory (or managed memory) that belongs to device `dev`, the
+// current device: the kernel runs there, with no peer mapping set up.
+bool on_device(const void *ptr, int dev) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
+  return attr.device == dev;
 }
 
 }  // namespace
@@ -82,9 +88,16 @@ extern "C" int hsga_run_generations_noalloc(const hsga_config *cfg, uint64_t gen
   const RunParams p = params_from_config(cfg);
   const bool tracked = cfg->surface_policy != HSGA_NONE;
   if (p.islands > kNoAllocMaxIslands) return HSGA_ERR_INVALID_ARG;
-  if (!trait || !on_device(trait)) return HSGA_ERR_INVALID_ARG;
-  if (tracked && (!surf || !on_device(surf))) return HSGA_ERR_INVALID_ARG;
-  if (generation + n_generations > kNoAllocMaxGeneration) return HSGA_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HSGA_ERR_CUDA;
+  }
+  if (!trait || !on_device(trait, dev)) return HSGA_ERR_INVALID_ARG;
+  if (tracked && (!surf || !on_device(surf, dev))) return HSGA_ERR_INVALID_ARG;
+  // written so that no sum can wrap around
+  if (generation > kNoAllocMaxGeneration || n_generations > kNoAllocMaxGeneration - generation)
+    return HSGA_ERR_INVALID_ARG;
   if (n_generations == 0) return HSGA_OK;
   ResidentPlan plan;
   if (!resident_plan(p, &plan)) return HSGA_ERR_UNSUPPORTED;

@@ -1,10 +1,13 @@
 """Batched runs: many independent runs of uneven shape and configuration
 advanced together (one launch per tick, ticks replayed from CUDA graphs,
-runs admitted between calls) must each equal the same configuration run
-alone on its own grid, bit for bit, and a sampled end state must equal the
-oracle's sampling of that population."""
+runs admitted between calls) must each equal the oracle's run of the same
+configuration, and the same configuration run alone on its own grid, bit
+for bit, and a sampled end state must equal the oracle's sampling of that
+population."""
 import numpy as np
 import pytest
+
+from conftest import oracle_config
 
 pytestmark = pytest.mark.gpu
 
@@ -46,8 +49,10 @@ def alone(hb, gens, kw):
         return g.population()
 
 
-def test_batch_runs_equal_runs_alone(hb):
+def test_batch_runs_equal_oracle_and_runs_alone(hb, orc, oracle_pool):
     runs = mixed_runs(1, 24)
+    want = [oracle_pool.submit(orc.run, oracle_config(orc, kw), None, None, 0, gens)
+            for gens, kw in runs]
     with hb.Batch() as b:
         ids = [b.add(gens, **kw) for gens, kw in runs[:16]]
         b.run(100)                                         # first wave
@@ -59,6 +64,9 @@ def test_batch_runs_equal_runs_alone(hb):
             info = b.info(rid)
             assert info["done"] and info["generation"] == gens
             t, s = b.population(rid)
+            ot, os_, _ = want[ids.index(rid)].result()
+            assert np.array_equal(t, ot), ("oracle", rid, kw)
+            assert np.array_equal(s, os_), ("oracle", rid, kw)
             wt, ws = alone(hb, gens, kw)
             assert np.array_equal(t, wt), (rid, kw)
             assert np.array_equal(s, ws), (rid, kw)

@@ -74,7 +74,7 @@ def start_state(rng, c, kw):
         trait = rng.normal(0, 1, c.agents).astype(np.float32).view(np.uint32)
     else:
         trait = rng.integers(0, 6, c.agents).astype(np.uint32)
-    surf = rng.integers(0, 2**63, c.agents * c.words, dtype=np.uint64)
+    surf = rng.integers(0, 2**64 - 1, c.agents * c.words, dtype=np.uint64, endpoint=True)
     if kw["policy"] == "none":
         surf[:] = 0
     return trait, surf

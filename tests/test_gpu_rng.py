@@ -39,3 +39,18 @@ def test_two_to_the_24_counters(hb, orc):
 def test_reserved_and_extreme_counters(hb, orc, c0, c1, c2, c3):
     got = device_sweep(hb, 7, c0, 65536, c1, c2, c3)
     assert np.array_equal(got, orc.philox_sweep(7, c0, 65536, c1, c2, c3))
+
+
+def test_throughput_kernel_draws_the_same_blocks(hb, orc):
+    """The kernel that measures the generator's throughput evaluates the same
+    blocks as the oracle: per thread, the xor of every word of its blocks."""
+    import torch
+    threads, m, c2, c3 = 300, 37, 0xABCDEF, 9          # a ragged block, m not a multiple of 4
+    seed = 0x0123456789ABCDEF
+    out = torch.zeros(threads, dtype=torch.int32, device="cuda")
+    hb.hsga_philox_throughput(seed, threads, m, c2, c3, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    for t in list(range(0, threads, 7)) + [threads - 1]:
+        want = np.bitwise_xor.reduce(orc.philox_sweep(seed, 0, m, t, c2, c3).reshape(-1))
+        assert got[t] == want, t

@@ -1,8 +1,12 @@
 """Continuous batching: requests that arrive while others run are admitted
 as memory frees up, their work overlaps on the device, and every result is
-the same as running the request alone (bit-exact sampled surfaces)."""
+the same as running the request alone (bit-exact sampled surfaces); the
+smaller requests' results also equal the oracle's run and sampling of the
+same request."""
 import numpy as np
 import pytest
+
+from conftest import oracle_config
 
 pytestmark = pytest.mark.gpu
 
@@ -17,10 +21,22 @@ def hb():
     return binding
 
 
-def test_served_results_equal_alone_under_memory_cap(hb):
+def oracle_result(config, generations, k):
+    """The oracle's run of one request from founders and its sample (runs in
+    a worker process)."""
+    import oracle
+    c = oracle_config(oracle, config)
+    t, s, _ = oracle.run(c, generations=generations)
+    return oracle.sample(c, t, s, generations, k)
+
+
+def test_served_results_equal_alone_and_oracle_under_memory_cap(hb, orc, oracle_pool):
     from paper_2404_10861_gb300 import serve
     reqs = serve.poisson_requests(24, rate=4000.0, seed=5, gen_scale=50,
                                   agents_range=(1024, 65536), sample_k=64)
+    small = {r.rid: oracle_pool.submit(oracle_result, r.config, r.generations, r.sample_k)
+             for r in reqs if r.agents * r.generations <= 3 * 10**7}
+    assert len(small) >= 8
     biggest = max(hb.hsga_run_footprint(hb.make_config(**r.config)) for r in reqs)
     cap = biggest               # the largest request only fits alone: admission must wait
     res_b, st_b = serve.serve(reqs, memory_cap=cap, slice_ticks=64)
@@ -34,5 +50,9 @@ def test_served_results_equal_alone_under_memory_cap(hb):
         assert np.array_equal(r.words, a.words), r.rid
         assert np.array_equal(r.where, a.where), r.rid
         assert r.finished >= r.admitted >= r.arrival - 1e-6
+        if r.rid in small:
+            ow, owhere = small[r.rid].result()
+            assert np.array_equal(r.words, ow), ("oracle", r.rid)
+            assert np.array_equal(r.where, owhere), ("oracle", r.rid)
     summ = serve.summarize(res_b, st_b)
     assert summ["latency_p99_s"] >= summ["latency_p50_s"] > 0

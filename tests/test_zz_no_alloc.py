@@ -80,3 +80,38 @@ def test_noalloc_rejects_oversized_grid_and_host_planes(hb):
     with pytest.raises(hb.HsgaError) as e:
         hb.hsga_run_generations_noalloc(small, 0, 1, th, sh)
     assert e.value.status == -1
+
+
+def test_noalloc_rejects_generation_counts_that_wrap(hb):
+    """G + n is checked without forming a sum that could wrap around in 64
+    bits: a G near 2^64 with one more generation must be refused, not run at
+    a truncated generation."""
+    import torch
+    cfg = hb.make_config(rows=4, cols=4, n=32)
+    t = torch.zeros(512, dtype=torch.int32, device="cuda")
+    s = torch.zeros(512, dtype=torch.int64, device="cuda")
+    for G, n in ((2**64 - 1, 1), (2**63, 2**63), (1, 2**64 - 1), (2**32 - 65, 1)):
+        with pytest.raises(hb.HsgaError) as e:
+            hb.hsga_run_generations_noalloc(cfg, G, n, t, s)
+        assert e.value.status == -1, (G, n)
+    hb.hsga_run_generations_noalloc(cfg, 2**32 - 66, 1, t, s)   # the largest G + n allowed
+
+
+def test_noalloc_planes_must_be_on_the_current_device(hb):
+    """The scratch array's address is the current device's, so planes that
+    live on another device are refused before any launch.  With one GPU the
+    current device's own planes are accepted; with two, planes on device 1
+    are refused while device 0 is current."""
+    import torch
+    cfg = hb.make_config(rows=4, cols=4, n=32)
+    torch.cuda.set_device(0)
+    t0 = torch.zeros(512, dtype=torch.int32, device="cuda:0")
+    s0 = torch.zeros(512, dtype=torch.int64, device="cuda:0")
+    hb.hsga_run_generations_noalloc(cfg, 0, 3, t0, s0)
+    if torch.cuda.device_count() < 2:
+        return
+    t1 = torch.zeros(512, dtype=torch.int32, device="cuda:1")
+    s1 = torch.zeros(512, dtype=torch.int64, device="cuda:1")
+    with pytest.raises(hb.HsgaError) as e:
+        hb.hsga_run_generations_noalloc(cfg, 0, 3, t1, s1)
+    assert e.value.status == -1
