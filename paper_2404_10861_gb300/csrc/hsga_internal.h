@@ -12,6 +12,8 @@ namespace hsga {
 
 constexpr int kStreamThreads = 256;     // streamed kernel block: 8 warps
 constexpr int kStreamBlocksPerSM = 3;   // 24 resident warps per SM (<= 80 registers)
+constexpr int kStagedThreads = 256;     // staged streamed kernel (n = 32) block: 8 warps
+constexpr int kStagedBlocksPerSM = 4;   // 32 resident warps per SM (<= 64 registers)
 constexpr int kResidentThreads = 128;   // resident kernel block: 4 warps
 constexpr uint32_t kSampleSmemMax = 12288;  // largest k sampled by the shared-memory kernel
 constexpr uint64_t kWaitNs = 1000000000ull; // bounded device wait: 1 s
@@ -28,6 +30,13 @@ struct ResidentPlan {
 cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
                                  const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
                                  uint64_t *sout, int *err, cudaStream_t stream);
+
+// The same generation for 32-agent islands with the parents staged in shared
+// memory by bulk asynchronous copies (hsga_staged.cu); waits report
+// timeouts in err.
+cudaError_t launch_step_staged(const RunParams &p, uint32_t G, bool do_mig, const uint32_t *tin,
+                               const uint64_t *sin, uint32_t *tout, uint64_t *sout, int *err,
+                               cudaStream_t stream);
 
 // Chooses the resident tile (smallest islands-per-warp whose cooperative
 // grid is co-resident).  Returns false when the grid does not fit on chip.

@@ -90,10 +90,12 @@ static void launch_streamed_t(const RunParams &p, const Deposit &dep, uint32_t G
 cudaError_t launch_step_streamed(const RunParams &p, uint32_t G, bool do_mig,
                                  const uint32_t *tin, const uint64_t *sin, uint32_t *tout,
                                  uint64_t *sout, int *err, cudaStream_t stream) {
+  // 32-agent islands (the paper's shape): parents staged in shared memory
+  if (p.n == 32) return launch_step_staged(p, G, do_mig, tin, sin, tout, sout, err, stream);
   const Deposit dep = deposit_for(p, G);
   const bool tracked = p.policy != HSGA_NONE;
   const bool t2 = p.tournament == 2;
-  (void)err;  // the streamed kernel has no waits
+  (void)err;  // the register kernel has no waits
 #define HSGA_LAUNCH(AP_, TR_, T2_, NN_) \
   launch_streamed_t<AP_, TR_, T2_, NN_>(p, dep, G, do_mig, tin, sin, tout, sout, stream)
 #define HSGA_LAUNCH_T(AP_, NN_)                         \
