@@ -13,7 +13,7 @@ namespace hsga {
 constexpr int kStreamThreads = 256;     // streamed kernel block: 8 warps
 constexpr int kStreamBlocksPerSM = 3;   // 24 resident warps per SM (<= 80 registers)
 constexpr int kStagedThreads = 256;     // staged streamed kernel (n = 32) block: 8 warps
-constexpr int kStagedBlocksPerSM = 4;   // 32 resident warps per SM (<= 64 registers)
+constexpr int kStagedBlocksPerSM = 3;   // 24 resident warps per SM (<= 85 registers)
 constexpr int kResidentThreads = 128;   // resident kernel block: 4 warps
 constexpr uint32_t kSampleSmemMax = 12288;  // largest k sampled by the shared-memory kernel
 constexpr uint64_t kWaitNs = 1000000000ull; // bounded device wait: 1 s

@@ -20,6 +20,18 @@
 // latest of N, E, S, W wins a shared slot).  Children go straight to the
 // child planes with streaming stores.
 //
+// The counter words of the replication blocks other than the island are
+// fixed for a launch (child slot = lane, generation, purpose), and so are
+// those of the migration blocks (slot word by the lane's role, generation,
+// purpose): each lane evaluates the island-independent part of rounds 1-3
+// once per launch (philox_head3), leaving 16 of the 20 multiplies per block.
+//
+// Consecutive generations overlap at the launch boundary (programmatic
+// dependent launch): a launch lets the next one be scheduled as soon as it
+// starts, and the next one initialises its barriers and generator heads,
+// then waits (griddepcontrol.wait) for this launch to complete and its
+// writes to be visible before it touches either population plane.
+//
 // Waits on a stage are bounded (1 s of %globaltimer): on expiry the warp
 // records HSGA_ERR_WAIT_TIMEOUT in the grid's error word, waits (bounded
 // again) for its own copies still in flight, and leaves.
@@ -100,6 +112,47 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if ((i & 63u) == 0 && now_ns() - t0 > kWaitNs) return false;
   }
   return false;
+}
+
+// a1 + a2 draws of a group (the register kernel's group_migration with the
+// migration blocks' deep heads and branch-free neighbour indices): lane
+// 5p+r (r < 4) draws the emigrant block of island isl0+p's neighbour in
+// direction r and gathers that emigrant from the parent planes when it is
+// aimed at isl0+p; lane 5p+4 draws isl0+p's placement block and builds its
+// landing plan (byte 3-d: slot of the direction-d immigrant, 0xFF: none).
+template <bool TRACKED>
+__device__ __forceinline__ void group_migration_staged(const RunParams &p, const PhiloxHead3 &mh,
+                                                       uint32_t lane, uint32_t isl0,
+                                                       const uint32_t *__restrict__ tin,
+                                                       const uint64_t *__restrict__ sin,
+                                                       GroupMigration &gm) {
+  const uint32_t pi = lane / 5u, role = lane - pi * 5u;
+  const bool valid = lane < 5u * kGroup;
+  const uint32_t isl = isl0 + (valid ? pi : 0u);
+  uint32_t r = fastdiv(p.cols_div, isl), c = isl - r * p.cols;
+  const uint32_t up = (r == 0u ? p.rows : r) - 1u, down = (r + 1u == p.rows) ? 0u : r + 1u;
+  const uint32_t left = (c == 0u ? p.cols : c) - 1u, right = (c + 1u == p.cols) ? 0u : c + 1u;
+  r = role == 0u ? up : (role == 2u ? down : r);
+  c = role == 1u ? right : (role == 3u ? left : c);
+  const uint32_t src = r * p.cols + c;  // role 4: the island itself
+  const Words4 m = philox_tail3<true>(p, mh, src);
+  const bool arrive = valid && role < 4u && (m.y >> 30) == ((role + 2u) & 3u);
+  gm.it = 0;
+  gm.is = 0;
+  if (arrive) {
+    const uint32_t a = src * 32u + (m.x >> 27);
+    gm.it = __ldg(tin + a);
+    if constexpr (TRACKED) gm.is = __ldg(sin + a);
+  }
+  const uint32_t arrivals = __ballot_sync(kFull, arrive);
+  const uint32_t bits = (arrivals >> (5u * pi)) & 0xFu;
+  // slots (< 32) in byte d, 0xFF in the bytes of directions with no arrival
+  // (the multiply spreads bit d of `miss` to bit 8d without carries), then the
+  // byte order reversed
+  const uint32_t miss = ~bits & 0xFu;
+  const uint32_t fwd = (m.x >> 27) | ((m.y >> 27) << 8) | ((m.z >> 27) << 16) |
+                       ((m.w >> 27) << 24) | (((miss * 0x00204081u) & 0x01010101u) * 0xFFu);
+  gm.plan = (role == 4u && valid) ? __byte_perm(fwd, 0u, 0x0123u) : 0xFFFFFFFFu;
 }
 
 // a2 for a staged group: lane 5p+r (r < 4) holds the immigrant of island p
@@ -186,25 +239,35 @@ __global__ void __launch_bounds__(kStagedThreads, kStagedBlocksPerSM)
       bulk_load(s_surf[wib][st], sin + (size_t)grp * kStageAgents, kSurfBytes, &bar[st]);
   };
 
+  // the next launch may be scheduled now; it waits below for this one
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_init_fence();
+  }
+  const PhiloxHead3 head = philox_head3(p.k0, p.k1, lane, G, kPurposeReplicate);
+  const PhiloxHead3 mhead = philox_head3(p.k0, p.k1, lane % 5u == 4u ? kSlotImmigrant
+                                                                     : kSlotEmigrant,
+                                         G, kPurposeMigration);
+  // the previous launch (which wrote this launch's parents and read the
+  // plane this one writes) has completed and its writes are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (lane == 0) {
     if (warp < nfull) issue(warp, 0);
     if (warp + nwarps < nfull) issue(warp + nwarps, 1);
   }
   __syncwarp();
 
-  const PhiloxHead head = philox_head(p.k0, p.k1, lane, G, kPurposeReplicate);
   uint32_t k = 0;
   for (uint32_t grp = warp; grp < nfull; grp += nwarps, ++k) {
     const uint32_t st = k & 1u, parity = (k >> 1) & 1u;
     const uint32_t isl0 = grp * kGroup;
     GroupMigration gm;
-    if constexpr (MIG) group_migration<TRACKED, true, 32>(p, isl0, G, tin, sin, gm);
+    if constexpr (MIG) group_migration_staged<TRACKED>(p, mhead, lane, isl0, tin, sin, gm);
     Words4 w[kGroup];
 #pragma unroll
-    for (uint32_t i = 0; i < kGroup; ++i) w[i] = philox_tail<true>(p, head, isl0 + i);
+    for (uint32_t i = 0; i < kGroup; ++i) w[i] = philox_tail3<true>(p, head, isl0 + i);
     if (!__all_sync(kFull, mbar_wait(&bar[st], parity))) {
       // give up: record the timeout, wait (bounded) for this warp's copies
       // still in flight, leave
@@ -222,15 +285,16 @@ __global__ void __launch_bounds__(kStagedThreads, kStagedBlocksPerSM)
       land_staged<TRACKED>(gm, lane, tr, sr);
       __syncwarp();
     }
+    uint32_t *to = tout + (size_t)isl0 * 32u + lane;
+    uint64_t *so = TRACKED ? sout + (size_t)isl0 * 32u + lane : sout;
 #pragma unroll
     for (uint32_t i = 0; i < kGroup; ++i) {
       uint32_t ct;
       uint64_t cs;
       replicate_staged<TRACKED, T2, TWO, DEL>(p, dep, lane, isl0 + i, G, w[i], tr + 32u * i,
                                               sr + (TRACKED ? 32u * i : 0u), ct, cs);
-      const size_t a = (size_t)(isl0 + i) * 32u + lane;
-      __stcs(tout + a, ct);
-      if constexpr (TRACKED) __stcs(sout + a, cs);
+      __stcs(to + 32u * i, ct);
+      if constexpr (TRACKED) __stcs(so + 32u * i, cs);
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
     if (lane == 0 && grp + 2u * nwarps < nfull) issue(grp + 2u * nwarps, st);
@@ -262,8 +326,18 @@ void launch_staged_t(const RunParams &p, const Deposit &dep, uint32_t G, const u
   const uint32_t need = (groups + kWarpsPerBlock - 1) / kWarpsPerBlock;
   int b = staged_blocks<TRACKED, T2, TWO, DEL, MIG>();
   if ((uint32_t)b > need) b = (int)need;
-  step_staged_kernel<TRACKED, T2, TWO, DEL, MIG>
-      <<<b, kStagedThreads, 0, stream>>>(p, dep, G, tin, sin, tout, sout, err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)b);
+  cfg.blockDim = dim3(kStagedThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, step_staged_kernel<TRACKED, T2, TWO, DEL, MIG>, p, dep, G, tin, sin,
+                     tout, sout, err);
 }
 
 template <bool TRACKED, bool T2>
