@@ -65,7 +65,9 @@ def measured_peaks():
 
 KERNEL_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",
                   "paper_2404_10861_gb300/csrc/hsga_island.cuh",
-                  "paper_2404_10861_gb300/csrc/hsga_kernels.cu"]
+                  "paper_2404_10861_gb300/csrc/hsga_internal.h",
+                  "paper_2404_10861_gb300/csrc/hsga_kernels.cu",
+                  "paper_2404_10861_gb300/csrc/hsga_staged.cu"]
 PROFILE = os.path.join(ROOT, "profiles", "step_streamed_wafer.md")
 FREE_RUNNING_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",
                         "paper_2404_10861_gb300/csrc/hsga_island.cuh",
@@ -387,7 +389,7 @@ def run_ours(args):
     reps = AGENTS * GENS_PER_STEP * args.steps * world
     value = reps / (elapsed_ms / 1e3)
 
-    # roofline of the dominant kernel (the streamed generation kernel)
+    # roofline of the dominant kernel (the staged generation kernel)
     per_launch_s = gen_ms / 1e3 / (GENS_PER_STEP * args.steps)
     alu_peak = philox_peak(stream)
     achieved = BYTES_PER_LAUNCH / per_launch_s / 1e9
@@ -442,12 +444,12 @@ def run_ours(args):
                 "dtype": "u32", "data": "synthetic",
                 "config": config_json(world),
                 "step": {"generations": GENS_PER_STEP, "sample_genomes": SAMPLE_K,
-                         "kernel": "step_streamed_kernel (one generation per launch)"},
+                         "kernel": "step_staged_kernel (one generation per launch)"},
                 "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                             "kernel": "step_streamed_kernel", "peak_kind": peak_kind,
+                             "kernel": "step_staged_kernel", "peak_kind": peak_kind,
                              "algorithmic_bytes_per_launch": BYTES_PER_LAUNCH,
                              "avg_launch_us": per_launch_s * 1e6},
                 "alu": alu_roofline(value / world, alu_peak),
@@ -682,6 +684,72 @@ def run_async_wafer(args, mode="async"):
                       "data": "synthetic"}), flush=True)
 
 
+def run_wafer_full(args, mode):
+    """The wafer-shaped workload as the paper runs it: free-running migration
+    on the full 512 x 1024-island grid for args.full_gens generations
+    (1,000,000 by default) from founders, then a 10,000-genome sample and its
+    phylogeny reconstructed on the GPU (hsga_reconstruct) among the sampled
+    genomes that share the modal deposition counter (free-running genomes
+    carry their own counters).  The paper's own figure for this regime (a
+    different machine, workload and genome) is context only."""
+    import torch
+    from paper_2404_10861_gb300 import _build, binding as hb
+    _build.build()
+    torch.cuda.set_device(0)
+    hb.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    K = 512
+    total = args.full_gens
+    with hb.Grid(stream=stream.cuda_stream, mode=mode, seed=1, **WORKLOAD) as g:
+        g.run(K)                                   # warm-up launch (counted in the run)
+        g.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            done = K
+            while done < total:
+                m = min(K, total - done)
+                g.run(m)
+                done += m
+            e1.record(stream)
+            e1.synchronize()
+        wall = time.perf_counter() - t0
+        gpu_s = e0.elapsed_time(e1) / 1e3
+        timed = total - K
+        words, where = g.sample(SAMPLE_K)
+        trait, _ = g.population()
+    T = words[:, 3].astype(np.int64)
+    vals, counts = np.unique(T, return_counts=True)
+    Tm = int(vals[np.argmax(counts)])
+    pick = T == Tm
+    surf = words[pick, 1].astype(np.uint64) | (words[pick, 2].astype(np.uint64) << np.uint64(32))
+    t1 = time.perf_counter()
+    parent, tm, leaf = hb.hsga_reconstruct(surf, "tilted", 1, 2, Tm, stream=stream.cuda_stream)
+    rec_s = time.perf_counter() - t1
+    root = parent < 0
+    sbl = int((tm[~root] - tm[parent[~root]]).sum())
+    print(json.dumps({
+        "metric": "agent replications/sec", "unit": "agent replications/s",
+        "workload": f"wafer-shaped island GA, free-running migration ({mode}), "
+                    f"512x1024 islands x 32 agents, {total} generations from founders",
+        "config": dict(WORKLOAD, mode=mode, generations=total, generations_per_launch=K),
+        "value": AGENTS * timed / gpu_s, "generations_per_s": timed / gpu_s,
+        "seconds_for_1M_generations": 1e6 * gpu_s / timed, "wall_s": wall,
+        "clocks": clk.summary(),
+        "sample": {"genomes": SAMPLE_K, "counter_min": int(T.min()), "counter_max": int(T.max()),
+                   "counter_modal": Tm, "genomes_at_modal_counter": int(pick.sum()),
+                   "distinct_counters": int(len(vals))},
+        "reconstruction": {"genomes": int(pick.sum()), "nodes": int(len(parent)),
+                           "sum_branch_length": sbl, "seconds": rec_s,
+                           "engine": "hsga_reconstruct (GPU trie)"},
+        "mean_trait": float(trait.mean()),
+        "paper_context": "Cerebras CS-2, 750x750 PEs x 32 agents (18.0M), tournament 5, float "
+                         "fitness: 1M generations in slightly under a minute (17,688 "
+                         "generations/s); a different machine and workload",
+        "dtype": "u32", "data": "synthetic"}), flush=True)
+
+
 def run_reconstruct(args):
     """Phylogeny reconstruction from sampled surfaces of the wafer-shaped grid
     after 1,000 generations: the GPU trie (hsga_reconstruct, inputs and
@@ -769,7 +837,7 @@ def main():
                          "(no timing); used for ncu captures")
     ap.add_argument("--workload", default="wafer",
                     choices=["wafer", "tiny", "mid", "batched", "served", "async", "buffered",
-                             "reconstruct"],
+                             "reconstruct", "async-full", "buffered-full"],
                     help="wafer: the benchmark line; the others: informational lines")
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--memory-cap-mb", type=int, default=2048,
@@ -779,6 +847,8 @@ def main():
                          "(default 100 batched, 10 served)")
     ap.add_argument("--slices", type=int, nargs="+", default=[1, 8, 64, 512],
                     help="async workload: generations per launch to measure")
+    ap.add_argument("--full-gens", type=int, default=1_000_000,
+                    help="async-full / buffered-full workloads: generations from founders")
     ap.add_argument("--async-gens", type=int, default=2048,
                     help="async workload: timed generations per slice length")
     args = ap.parse_args()
@@ -787,6 +857,9 @@ def main():
         return
     if args.workload == "reconstruct":
         run_reconstruct(args)
+        return
+    if args.workload in ("async-full", "buffered-full"):
+        run_wafer_full(args, args.workload.split("-")[0])
         return
     if args.workload == "batched":
         run_batched(args)

@@ -290,71 +290,6 @@ __device__ __forceinline__ PhiloxHead philox_head(uint32_t k0, uint32_t k1, uint
                     (uint32_t)p0};
 }
 
-// A deeper head for the same fixed counter words.  Word 1 (the island) enters
-// round 1 only through output word 0, so in round 2 the multiply of word 2
-// and in round 3 the multiply of word 0 still see only fixed words: both are
-// hoisted out of the per-island work, which keeps 16 of the block's 20
-// multiplies and 18 of its 20 xor steps per island.  Same block as
-// philox(k0, k1, c0, island, c2, c3) for every island.
-struct PhiloxHead3 {
-  uint32_t x0;   // high(M1 c2) ^ k0: round-1 word 0 before the island
-  uint32_t a3;   // round-1 word 3
-  uint32_t b1;   // round-2 word 1
-  uint32_t h2;   // high(M0 b0) ^ round-3 key 1: round-3 word 2 before b3
-  uint32_t c3;   // round-3 word 3
-};
-
-__host__ __device__ __forceinline__ uint32_t mul_hi32(uint32_t a, uint32_t b) {
-  return (uint32_t)(((uint64_t)a * b) >> 32);
-}
-
-__host__ __device__ __forceinline__ PhiloxHead3 philox_head3(uint32_t k0, uint32_t k1,
-                                                             uint32_t c0, uint32_t c2,
-                                                             uint32_t c3) {
-  // round 1: words 1 and 3 do not depend on the island, word 2 neither
-  const uint32_t a1 = kPhiloxM1 * c2;
-  const uint32_t a2 = mul_hi32(kPhiloxM0, c0) ^ c3 ^ k1;
-  const uint32_t a3 = kPhiloxM0 * c0;
-  // round 2: the multiply of word 2 (a2) is fixed
-  const uint32_t b0 = mul_hi32(kPhiloxM1, a2) ^ a1 ^ (k0 + kPhiloxW0);
-  const uint32_t b1 = kPhiloxM1 * a2;
-  // round 3: the multiply of word 0 (b0) is fixed
-  return PhiloxHead3{mul_hi32(kPhiloxM1, c2) ^ k0, a3, b1,
-                     mul_hi32(kPhiloxM0, b0) ^ (k1 + 2u * kPhiloxW1), kPhiloxM0 * b0};
-}
-
-// The block for island c1 after a deep head: rounds 2-3 on the island-
-// dependent words, then rounds 4-10.  RK: round keys from the parameter
-// block (device), else derived from the key.
-template <bool RK>
-__host__ __device__ __forceinline__ Words4 philox_tail3(const RunParams &p, const PhiloxHead3 &h,
-                                                        uint32_t c1_in) {
-  const uint32_t a0 = h.x0 ^ c1_in;
-  const uint64_t q = (uint64_t)a0 * kPhiloxM0;  // round 2, word 0
-  const uint32_t k1r1 = RK ? p.rk1[1] : p.k1 + kPhiloxW1;
-  const uint32_t b2 = (uint32_t)(q >> 32) ^ h.a3 ^ k1r1;
-  const uint32_t b3 = (uint32_t)q;
-  const uint64_t r = (uint64_t)b2 * kPhiloxM1;  // round 3, word 2
-  const uint32_t k0r2 = RK ? p.rk0[2] : p.k0 + 2u * kPhiloxW0;
-  uint32_t c0 = (uint32_t)(r >> 32) ^ h.b1 ^ k0r2, c1 = (uint32_t)r, c2 = h.h2 ^ b3, c3 = h.c3;
-#ifdef __CUDA_ARCH__
-#pragma unroll
-#endif
-  for (int rr = 3; rr < 10; ++rr) {
-    const uint32_t k0 = RK ? p.rk0[rr] : p.k0 + (uint32_t)rr * kPhiloxW0;
-    const uint32_t k1 = RK ? p.rk1[rr] : p.k1 + (uint32_t)rr * kPhiloxW1;
-    const uint64_t p0 = (uint64_t)c0 * kPhiloxM0;
-    const uint64_t p1 = (uint64_t)c2 * kPhiloxM1;
-    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-    c0 = n0;
-    c1 = (uint32_t)p1;
-    c2 = n2;
-    c3 = (uint32_t)p0;
-  }
-  return Words4{c0, c1, c2, c3};
-}
-
 // Rounds 2-10 after a precomputed head; RK as below.
 template <bool RK>
 __device__ __forceinline__ Words4 philox_tail(const RunParams &p, const PhiloxHead &h,

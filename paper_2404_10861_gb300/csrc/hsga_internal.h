@@ -13,7 +13,11 @@ namespace hsga {
 constexpr int kStreamThreads = 256;     // streamed kernel block: 8 warps
 constexpr int kStreamBlocksPerSM = 3;   // 24 resident warps per SM (<= 80 registers)
 constexpr int kStagedThreads = 256;     // staged streamed kernel (n = 32) block: 8 warps
-constexpr int kStagedBlocksPerSM = 3;   // 24 resident warps per SM (<= 85 registers)
+// 16 resident warps per SM (<= 128 registers) with two groups in flight per
+// warp: measured fastest at 16.8M agents (75.3 us per generation; 24 warps:
+// 78.7 us; 3-5 stages: 76.3-81.2 us).
+constexpr int kStagedBlocksPerSM = 2;
+constexpr uint32_t kStagedStages = 2;   // groups in flight per warp
 constexpr int kResidentThreads = 128;   // resident kernel block: 4 warps
 constexpr uint32_t kSampleSmemMax = 12288;  // largest k sampled by the shared-memory kernel
 constexpr uint64_t kWaitNs = 1000000000ull; // bounded device wait: 1 s

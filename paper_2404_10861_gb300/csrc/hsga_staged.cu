@@ -7,11 +7,11 @@
 // the surface update).  A persistent grid of warps walks the islands in
 // groups of six (the group of the island-group helpers: six islands' five
 // migration blocks fill 30 lanes of one warp-wide Philox evaluation).  Each
-// warp owns a two-stage ring in shared memory; one lane copies a whole
-// group's parents into a stage with cp.async.bulk (768 bytes of traits and
-// 1,536 bytes of surfaces, both contiguous in the island-major planes),
-// completing on that stage's mbarrier, two groups ahead of the one being
-// replicated.  The bytes in flight therefore cost no registers, and the
+// warp owns a ring of kStagedStages stages in shared memory; one lane copies
+// a whole group's parents into a stage with cp.async.bulk (768 bytes of
+// traits and 1,536 bytes of surfaces, both contiguous in the island-major
+// planes), completing on that stage's mbarrier, up to kStagedStages groups
+// ahead of the one being replicated.  The bytes in flight therefore cost no registers, and the
 // tournament reads the parents from shared memory: two 4-byte loads for the
 // candidates' fitness and one 8-byte load for the winner's surface per
 // child, where a register-resident island needs its own loads plus four
@@ -20,11 +20,9 @@
 // latest of N, E, S, W wins a shared slot).  Children go straight to the
 // child planes with streaming stores.
 //
-// The counter words of the replication blocks other than the island are
-// fixed for a launch (child slot = lane, generation, purpose), and so are
-// those of the migration blocks (slot word by the lane's role, generation,
-// purpose): each lane evaluates the island-independent part of rounds 1-3
-// once per launch (philox_head3), leaving 16 of the 20 multiplies per block.
+// The replication blocks' counter words other than the island (child slot =
+// lane, generation, purpose) are fixed for a launch, so each lane evaluates
+// round 1's island-independent part once per launch (philox_head).
 //
 // Consecutive generations overlap at the launch boundary (programmatic
 // dependent launch): a launch lets the next one be scheduled as soon as it
@@ -114,47 +112,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return false;
 }
 
-// a1 + a2 draws of a group (the register kernel's group_migration with the
-// migration blocks' deep heads and branch-free neighbour indices): lane
-// 5p+r (r < 4) draws the emigrant block of island isl0+p's neighbour in
-// direction r and gathers that emigrant from the parent planes when it is
-// aimed at isl0+p; lane 5p+4 draws isl0+p's placement block and builds its
-// landing plan (byte 3-d: slot of the direction-d immigrant, 0xFF: none).
-template <bool TRACKED>
-__device__ __forceinline__ void group_migration_staged(const RunParams &p, const PhiloxHead3 &mh,
-                                                       uint32_t lane, uint32_t isl0,
-                                                       const uint32_t *__restrict__ tin,
-                                                       const uint64_t *__restrict__ sin,
-                                                       GroupMigration &gm) {
-  const uint32_t pi = lane / 5u, role = lane - pi * 5u;
-  const bool valid = lane < 5u * kGroup;
-  const uint32_t isl = isl0 + (valid ? pi : 0u);
-  uint32_t r = fastdiv(p.cols_div, isl), c = isl - r * p.cols;
-  const uint32_t up = (r == 0u ? p.rows : r) - 1u, down = (r + 1u == p.rows) ? 0u : r + 1u;
-  const uint32_t left = (c == 0u ? p.cols : c) - 1u, right = (c + 1u == p.cols) ? 0u : c + 1u;
-  r = role == 0u ? up : (role == 2u ? down : r);
-  c = role == 1u ? right : (role == 3u ? left : c);
-  const uint32_t src = r * p.cols + c;  // role 4: the island itself
-  const Words4 m = philox_tail3<true>(p, mh, src);
-  const bool arrive = valid && role < 4u && (m.y >> 30) == ((role + 2u) & 3u);
-  gm.it = 0;
-  gm.is = 0;
-  if (arrive) {
-    const uint32_t a = src * 32u + (m.x >> 27);
-    gm.it = __ldg(tin + a);
-    if constexpr (TRACKED) gm.is = __ldg(sin + a);
-  }
-  const uint32_t arrivals = __ballot_sync(kFull, arrive);
-  const uint32_t bits = (arrivals >> (5u * pi)) & 0xFu;
-  // slots (< 32) in byte d, 0xFF in the bytes of directions with no arrival
-  // (the multiply spreads bit d of `miss` to bit 8d without carries), then the
-  // byte order reversed
-  const uint32_t miss = ~bits & 0xFu;
-  const uint32_t fwd = (m.x >> 27) | ((m.y >> 27) << 8) | ((m.z >> 27) << 16) |
-                       ((m.w >> 27) << 24) | (((miss * 0x00204081u) & 0x01010101u) * 0xFFu);
-  gm.plan = (role == 4u && valid) ? __byte_perm(fwd, 0u, 0x0123u) : 0xFFFFFFFFu;
-}
-
 // a2 for a staged group: lane 5p+r (r < 4) holds the immigrant of island p
 // from direction r when it arrives; the landing plan of island p (lane 5p+4,
 // byte 3-d: slot of direction d, 0xFF: none) says where.  The lane stores it
@@ -216,71 +173,81 @@ __device__ __forceinline__ void replicate_staged(const RunParams &p, const Depos
   else cs = 0;
 }
 
+constexpr uint32_t kStageBytes = kTraitBytes + kSurfBytes;  // 2304 per group
+constexpr uint32_t kStages = kStagedStages;
+constexpr size_t kRingBytes = (size_t)kWarpsPerBlock * kStages * kStageBytes;
+
 template <bool TRACKED, bool T2, bool TWO, bool DEL, bool MIG>
 __global__ void __launch_bounds__(kStagedThreads, kStagedBlocksPerSM)
     step_staged_kernel(RunParams p, Deposit dep, uint32_t G, const uint32_t *__restrict__ tin,
                        const uint64_t *__restrict__ sin, uint32_t *__restrict__ tout,
                        uint64_t *__restrict__ sout, int *__restrict__ err) {
-  __shared__ __align__(128) uint32_t s_trait[kWarpsPerBlock][2][kStageAgents];
-  __shared__ __align__(128) uint64_t s_surf[kWarpsPerBlock][2][TRACKED ? kStageAgents : 2];
-  __shared__ __align__(8) uint64_t s_bar[kWarpsPerBlock][2];
+  extern __shared__ __align__(128) unsigned char s_ring[];  // the ring (kRingBytes), padded
+  __shared__ __align__(8) uint64_t s_bar[kWarpsPerBlock][kStages];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const uint32_t warp = blockIdx.x * kWarpsPerBlock + wib;
   const uint32_t nwarps = gridDim.x * kWarpsPerBlock;
   const uint32_t nfull = p.islands / kGroup;
+  unsigned char *ring = s_ring + (size_t)wib * kStages * kStageBytes;
   uint64_t *bar = s_bar[wib];
   constexpr uint32_t kTx = kTraitBytes + (TRACKED ? kSurfBytes : 0u);
 
+  // stage st holds a group's traits (768 B) then its surfaces (1,536 B)
   auto issue = [&](uint32_t grp, uint32_t st) {  // one lane
+    unsigned char *dst = ring + st * kStageBytes;
     proxy_fence();
     mbar_expect_tx(&bar[st], kTx);
-    bulk_load(s_trait[wib][st], tin + (size_t)grp * kStageAgents, kTraitBytes, &bar[st]);
+    bulk_load(dst, tin + (size_t)grp * kStageAgents, kTraitBytes, &bar[st]);
     if constexpr (TRACKED)
-      bulk_load(s_surf[wib][st], sin + (size_t)grp * kStageAgents, kSurfBytes, &bar[st]);
+      bulk_load(dst + kTraitBytes, sin + (size_t)grp * kStageAgents, kSurfBytes, &bar[st]);
   };
 
   // the next launch may be scheduled now; it waits below for this one
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+#pragma unroll
+    for (uint32_t st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
     mbar_init_fence();
   }
-  const PhiloxHead3 head = philox_head3(p.k0, p.k1, lane, G, kPurposeReplicate);
-  const PhiloxHead3 mhead = philox_head3(p.k0, p.k1, lane % 5u == 4u ? kSlotImmigrant
-                                                                     : kSlotEmigrant,
-                                         G, kPurposeMigration);
+  const PhiloxHead head = philox_head(p.k0, p.k1, lane, G, kPurposeReplicate);
   // the previous launch (which wrote this launch's parents and read the
   // plane this one writes) has completed and its writes are visible
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (lane == 0) {
-    if (warp < nfull) issue(warp, 0);
-    if (warp + nwarps < nfull) issue(warp + nwarps, 1);
+#pragma unroll
+    for (uint32_t st = 0; st < kStages; ++st)
+      if (warp + st * nwarps < nfull) issue(warp + st * nwarps, st);
   }
   __syncwarp();
 
-  uint32_t k = 0;
-  for (uint32_t grp = warp; grp < nfull; grp += nwarps, ++k) {
-    const uint32_t st = k & 1u, parity = (k >> 1) & 1u;
+  uint32_t st = 0, phase = 0;  // ring position of the k-th group and its phase parity
+  for (uint32_t grp = warp; grp < nfull; grp += nwarps) {
     const uint32_t isl0 = grp * kGroup;
     GroupMigration gm;
-    if constexpr (MIG) group_migration_staged<TRACKED>(p, mhead, lane, isl0, tin, sin, gm);
+    if constexpr (MIG) group_migration<TRACKED, true, 32>(p, isl0, G, tin, sin, gm);
     Words4 w[kGroup];
 #pragma unroll
-    for (uint32_t i = 0; i < kGroup; ++i) w[i] = philox_tail3<true>(p, head, isl0 + i);
-    if (!__all_sync(kFull, mbar_wait(&bar[st], parity))) {
+    for (uint32_t i = 0; i < kGroup; ++i) w[i] = philox_tail<true>(p, head, isl0 + i);
+    if (!__all_sync(kFull, mbar_wait(&bar[st], phase))) {
       // give up: record the timeout, wait (bounded) for this warp's copies
-      // still in flight, leave
+      // still in flight (the groups issued into the ring from this one on),
+      // leave
       if (lane == 0) {
         atomicCAS(err, 0, kDevErrWaitTimeout);
-        mbar_wait(&bar[st], parity);
-        if (grp + nwarps < nfull) mbar_wait(&bar[st ^ 1u], ((k + 1) >> 1) & 1u);
+        uint32_t s2 = st, ph2 = phase;
+        for (uint32_t j = 0; j < kStages && grp + j * nwarps < nfull; ++j) {
+          mbar_wait(&bar[s2], ph2);
+          if (++s2 == kStages) {
+            s2 = 0;
+            ph2 ^= 1u;
+          }
+        }
       }
       __syncwarp();
       return;
     }
-    uint32_t *tr = s_trait[wib][st];
-    uint64_t *sr = s_surf[wib][st];
+    uint32_t *tr = (uint32_t *)(ring + st * kStageBytes);
+    uint64_t *sr = (uint64_t *)(ring + st * kStageBytes + kTraitBytes);
     if constexpr (MIG) {
       land_staged<TRACKED>(gm, lane, tr, sr);
       __syncwarp();
@@ -297,11 +264,38 @@ __global__ void __launch_bounds__(kStagedThreads, kStagedBlocksPerSM)
       if constexpr (TRACKED) __stcs(so + 32u * i, cs);
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
-    if (lane == 0 && grp + 2u * nwarps < nfull) issue(grp + 2u * nwarps, st);
+    if (lane == 0 && grp + kStages * nwarps < nfull) issue(grp + kStages * nwarps, st);
+    if (++st == kStages) {
+      st = 0;
+      phase ^= 1u;
+    }
   }
   // the last, partial group (fewer than six islands) on the register path
   if (p.islands % kGroup != 0u && warp == nfull % nwarps)
     partial_group<1, TRACKED, T2>(p, dep, G, MIG, nfull * kGroup, tin, sin, tout, sout);
+}
+
+// Shared memory requested per block: the ring, padded so that one block
+// more than kStagedBlocksPerSM does not fit on an SM.  Otherwise the next
+// generation's launch, scheduled early by programmatic dependent launch,
+// parks a block in the free slot that competes with the running blocks for
+// issue slots until it may start (107 us per generation at 16.8M agents
+// with a free slot, 75.3 us without).
+inline size_t staged_smem_bytes() {
+  static size_t bytes = 0;
+  if (bytes == 0) {
+    int dev = 0, per_sm = 0, per_block = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    size_t pad = (size_t)per_sm / (kStagedBlocksPerSM + 1) + 128;
+    pad = pad > (size_t)reserved ? pad - (size_t)reserved : pad;
+    size_t b = kRingBytes > pad ? kRingBytes : pad;
+    if (per_block > 0 && b > (size_t)per_block - 1024) b = kRingBytes;  // no room to pad
+    bytes = (b + 127) & ~(size_t)127;
+  }
+  return bytes;
 }
 
 template <bool TRACKED, bool T2, bool TWO, bool DEL, bool MIG>
@@ -311,8 +305,12 @@ int staged_blocks() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = staged_smem_bytes();
+    cudaFuncSetAttribute(step_staged_kernel<TRACKED, T2, TWO, DEL, MIG>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, step_staged_kernel<TRACKED, T2, TWO, DEL, MIG>, kStagedThreads, 0);
+        &per_sm, step_staged_kernel<TRACKED, T2, TWO, DEL, MIG>, kStagedThreads, smem);
+    if (per_sm > kStagedBlocksPerSM) per_sm = kStagedBlocksPerSM;
     blocks = sms * (per_sm > 0 ? per_sm : 1);
   }
   return blocks;
@@ -329,7 +327,7 @@ void launch_staged_t(const RunParams &p, const Deposit &dep, uint32_t G, const u
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)b);
   cfg.blockDim = dim3(kStagedThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = staged_smem_bytes();
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
