@@ -549,7 +549,7 @@ def run_batched(args):
     torch.cuda.set_device(0)
     hb.use_torch_allocator()
     if args.gen_scale is None:
-        args.gen_scale = 100
+        args.gen_scale = 1
     runs = batched_runs(args.gen_scale)
     reps = sum(g * kw["rows"] * kw["cols"] * kw["n"] for g, kw in runs)
     stream = torch.cuda.Stream()
@@ -596,12 +596,14 @@ def run_served(args):
     torch.cuda.set_device(0)
     hb.use_torch_allocator()
     if args.gen_scale is None:
-        args.gen_scale = 10
+        args.gen_scale = 1
     rate = 20.0 * args.gen_scale      # keeps the offered load of the full-size stream
     reqs = serve.poisson_requests(args.requests, rate, seed=5, gen_scale=args.gen_scale)
     offered = sum(r.agents * r.generations for r in reqs) / reqs[-1].arrival
     stream = torch.cuda.Stream()
-    cap = args.memory_cap_mb * 2**20
+    # the device's own memory is the cap unless one is given
+    cap = (args.memory_cap_mb * 2**20 if args.memory_cap_mb
+           else int(0.9 * torch.cuda.mem_get_info()[0]))
     res_b, st_b = serve.serve(reqs, memory_cap=cap, stream=stream.cuda_stream)
     res_a, st_a = serve.serve_alone(reqs, stream=stream.cuda_stream)
     same = sum(int(np.array_equal(a.words, b.words) and np.array_equal(a.where, b.where))
@@ -613,6 +615,8 @@ def run_served(args):
                     f"[1024, 4194304] (32 per island, near-square torus), generations "
                     f"log-uniform [1000, 100000] / {args.gen_scale}, random policy and "
                     f"adaptive flag, seed 5, 10,000-genome samples",
+        "admission": "size-aware: runs of >= 2^20 agents one at a time (first come, first "
+                     "served among them), smaller runs first come, first served as they fit",
         "offered_agent_replications_per_s": offered,
         "memory_cap_bytes": cap,
         "served": serve.summarize(res_b, st_b), "alone": serve.summarize(res_a, st_a),
@@ -839,12 +843,13 @@ def main():
                     choices=["wafer", "tiny", "mid", "batched", "served", "async", "buffered",
                              "reconstruct", "async-full", "buffered-full"],
                     help="wafer: the benchmark line; the others: informational lines")
-    ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
-    ap.add_argument("--memory-cap-mb", type=int, default=2048,
-                    help="served workload: device memory cap for admission")
+    ap.add_argument("--requests", type=int, default=2000, help="served workload: requests")
+    ap.add_argument("--memory-cap-mb", type=int, default=0,
+                    help="served workload: device memory cap for admission (default: 90%% of "
+                         "the device's free memory)")
     ap.add_argument("--gen-scale", type=int, default=None,
                     help="batched / served workloads: divide the generation budgets by this "
-                         "(default 100 batched, 10 served)")
+                         "(default 1: the stated budgets)")
     ap.add_argument("--slices", type=int, nargs="+", default=[1, 8, 64, 512],
                     help="async workload: generations per launch to measure")
     ap.add_argument("--full-gens", type=int, default=1_000_000,

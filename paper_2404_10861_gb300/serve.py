@@ -4,12 +4,21 @@ Requests (one island-model GA run each: grid, agents per island, policy,
 adaptation, generation budget) arrive over time.  The server keeps admitted
 runs resident on the device inside one batch (``hsga_batch_*``, which
 advances every active run by one generation per tick in one launch),
-admits waiting requests first-come-first-served whenever their device-memory
-footprint fits under a cap, advances the batch in slices of generations,
-and when a run finishes returns its sampled surfaces (step a7) and frees its
-memory.  Requests that arrive while others are on the GPU join between
-slices, so their work overlaps.  ``serve_alone`` is the reference policy:
-the same stream served one request at a time, each on its own grid.
+admits waiting requests whenever their device-memory footprint fits under a
+cap, advances the batch in slices of generations, and when a run finishes
+returns its sampled surfaces (step a7) and frees its memory.  Requests that
+arrive while others are on the GPU join between slices, so their work
+overlaps.
+
+Admission is size-aware.  A run of at least ``large_agents`` agents keeps
+the whole GPU busy on its own; at most ``max_large`` of those run at a time,
+first come first served among them, while smaller requests are admitted in
+arrival order as soon as they fit, never queueing behind a large one.  A
+large run then advances at nearly its speed alone (the small runs sharing
+its ticks add little work), and small runs, which alone would leave the GPU
+idle between their short generations, overlap with it.  ``serve_alone`` is
+the reference policy: the same stream served one request at a time, each on
+its own grid.
 
 Every run's result is the same whether it ran alone or in the mix (the batch
 engine is bit-identical to a lone grid); tests check that on sampled output.
@@ -93,34 +102,49 @@ def _wait_until(t0: float, rel: float):
         time.sleep(min(0.0005, max(0.0, rel - (time.perf_counter() - t0))))
 
 
-def serve(requests, memory_cap: int, slice_ticks: int = 256, stream=None):
-    """Continuous batching.  Returns (results, stats)."""
+def serve(requests, memory_cap: int, slice_ticks: int = 256, stream=None,
+          large_agents: int | None = 1 << 20, max_large: int = 1):
+    """Continuous batching with size-aware admission (module docstring);
+    large_agents=None admits every request first come, first served.
+    Returns (results, stats)."""
     pending = deque(sorted(requests, key=lambda r: r.arrival))
-    waiting: deque = deque()
+    waiting: list = []                 # arrived, not admitted, in arrival order
     running = {}                       # run id -> (request, admitted time, footprint)
     results = []
     in_use = 0
     peak_runs = 0
+    peak_large = 0
     blocked = 0                        # admissions deferred by the memory cap
+
+    def is_large(req):
+        return large_agents is not None and req.agents >= large_agents
+
     with hb.Batch(stream=stream) as batch:
         t0 = time.perf_counter()
         while pending or waiting or running:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            while waiting:
-                req = waiting[0]
+            large_now = sum(1 for req, _, _ in running.values() if is_large(req))
+            i = 0
+            while i < len(waiting):
+                req = waiting[i]
+                if is_large(req) and large_now >= max_large:
+                    i += 1                 # waits for the large slot; later requests may pass
+                    continue
                 fp = hb.hsga_run_footprint(hb.make_config(**req.config))
                 if fp > memory_cap:
                     raise ValueError(f"request {req.rid} needs {fp} bytes, over the cap")
                 if in_use + fp > memory_cap:
                     blocked += 1
-                    break
-                waiting.popleft()
+                    break                  # memory goes to requests in arrival order
+                waiting.pop(i)
                 rid = batch.add(req.generations, **req.config)
                 running[rid] = (req, time.perf_counter() - t0, fp)
                 in_use += fp
+                large_now += is_large(req)
             peak_runs = max(peak_runs, len(running))
+            peak_large = max(peak_large, large_now)
             if not running:
                 if pending:
                     _wait_until(t0, pending[0].arrival)
@@ -140,6 +164,7 @@ def serve(requests, memory_cap: int, slice_ticks: int = 256, stream=None):
         elapsed = time.perf_counter() - t0
         st = batch.stats()
     return results, {"elapsed_s": elapsed, "peak_concurrent_runs": peak_runs,
+                     "peak_concurrent_large_runs": peak_large,
                      "admissions_deferred": blocked, "kernel_launches": st["kernel_launches"],
                      "ticks": st["tick"]}
 

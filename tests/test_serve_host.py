@@ -160,3 +160,32 @@ def test_request_stream_follows_its_recipe():
     logs = np.log([r.agents for r in reqs])
     # log-uniform sizes: the median of log(agents) near the middle of the range
     assert abs(np.median(logs) - (math.log(1024) + math.log(4_194_304)) / 2) < 0.6
+
+
+def test_large_runs_one_at_a_time_and_small_ones_pass_them(fake):
+    """Size-aware admission: requests of at least large_agents agents run one
+    at a time in arrival order, and a small request that arrives behind a
+    waiting large one is admitted at once."""
+    big = 256            # 256 x 256 islands x 32 agents = 2.1M agents: large
+    reqs = [request(0, 0.0, big, 300), request(1, 0.0, big, 200), request(2, 0.0, 8, 50),
+            request(3, 0.0, big, 100), request(4, 0.0, 16, 80)]
+    results, stats = serve.serve(reqs, memory_cap=1 << 34, slice_ticks=64,
+                                 large_agents=1 << 20)
+    assert sorted(r.rid for r in results) == list(range(5))
+    assert stats["peak_concurrent_large_runs"] == 1
+    seeds = {r.config["seed"]: r for r in reqs}
+    adds = [seeds[ev[2]].rid for ev in fake.log if ev[0] == "add"]
+    assert adds.index(2) < adds.index(1) and adds.index(4) < adds.index(1)
+    assert [a for a in adds if reqs[a].agents >= 1 << 20] == [0, 1, 3]
+    live_large, rid_to_req = 0, {}
+    for ev in fake.log:                     # never two large runs live at once
+        if ev[0] == "add":
+            rid_to_req[ev[1]] = seeds[ev[2]]
+            live_large += rid_to_req[ev[1]].agents >= 1 << 20
+        elif ev[0] == "remove":
+            live_large -= rid_to_req[ev[1]].agents >= 1 << 20
+        assert live_large <= 1
+    # without the size rule, admission is first come, first served
+    serve.serve(reqs, memory_cap=1 << 34, slice_ticks=64, large_agents=None)
+    adds = [seeds[ev[2]].rid for ev in fake.log if ev[0] == "add"]
+    assert adds == [0, 1, 2, 3, 4]
