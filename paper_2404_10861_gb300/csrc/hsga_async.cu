@@ -46,18 +46,18 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
 // T_parent + 1.  t, s, T: this lane's genome, replaced by its child.  FLT:
 // binary32 fitness with Gaussian mutation amounts.  h: the head of the
 // replication block Philox(key; lane, *, G, 1), shared by all islands.
-template <bool TRACKED, bool T2, bool TWO, bool FLT = false>
+template <bool TRACKED, bool T2, bool TWO, bool FLT = false, int NN = 0>
 __device__ __forceinline__ void counter_step(const RunParams &p, const PhiloxHead &h,
                                              uint32_t lane, uint32_t isl, uint32_t G,
                                              uint32_t &t, uint64_t &s, uint32_t &T) {
-  const uint32_t n = p.n;
+  const uint32_t n = NN ? (uint32_t)NN : p.n;
   uint32_t pt[1] = {t}, pT[1] = {T};
   uint64_t ps[1] = {s};
   const Words4 w = philox_tail<true>(p, h, isl);
-  uint32_t best = uindex(w.x, n);
+  uint32_t best = uindex_nn<NN>(w.x, n);
   uint32_t fbest = fetch32<1>(pt, best);
   if (T2 || p.tournament >= 2) {
-    const uint32_t c = uindex(w.y, n);
+    const uint32_t c = uindex_nn<NN>(w.y, n);
     const uint32_t fc = fetch32<1>(pt, c);
     const bool pick = fitter<FLT>(fc, fbest);
     best = pick ? c : best;
@@ -70,7 +70,7 @@ __device__ __forceinline__ void counter_step(const RunParams &p, const PhiloxHea
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (c0 + q < p.tournament) {
-          const uint32_t c = uindex(ew[q], n);
+          const uint32_t c = uindex_nn<NN>(ew[q], n);
           const uint32_t fc = fetch32<1>(pt, c);
           if (fitter<FLT>(fc, fbest)) {
             best = c;
@@ -125,36 +125,41 @@ struct Octet {
   uint64_t s[IPW];
 };
 
-template <bool TRACKED, int IPW>
+// NN: agents per island known at compile time (32: the octet's planes are
+// one contiguous run of 32 IPW genomes, addressed from one base), or 0.
+template <bool TRACKED, int IPW, int NN = 0>
 __device__ __forceinline__ void load_octet(const RunParams &p, Octet<IPW> &o, uint32_t first,
                                            uint32_t lane, const uint32_t *tplane,
                                            const uint64_t *splane, const uint32_t *Tplane) {
   o.first = first;
+  const uint32_t n = NN ? (uint32_t)NN : p.n;
+  const size_t base = (size_t)first * n + lane;
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
     const uint32_t isl = first + k;
     o.live[k] = isl < p.islands;
     o.t[k] = o.T[k] = 0;
     o.s[k] = 0;
-    if (o.live[k] && lane < p.n) {
-      o.t[k] = tplane[isl * p.n + lane];
-      if constexpr (TRACKED) o.s[k] = splane[isl * p.n + lane];
-      o.T[k] = Tplane[isl * p.n + lane];
+    if (o.live[k] && (NN == 32 || lane < n)) {
+      o.t[k] = tplane[base + k * n];
+      if constexpr (TRACKED) o.s[k] = splane[base + k * n];
+      o.T[k] = Tplane[base + k * n];
     }
   }
 }
 
-template <bool TRACKED, int IPW>
+template <bool TRACKED, int IPW, int NN = 0>
 __device__ __forceinline__ void store_octet(const RunParams &p, const Octet<IPW> &o,
                                             uint32_t lane, uint32_t *tplane, uint64_t *splane,
                                             uint32_t *Tplane) {
+  const uint32_t n = NN ? (uint32_t)NN : p.n;
+  const size_t base = (size_t)o.first * n + lane;
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
-    const uint32_t isl = o.first + k;
-    if (o.live[k] && lane < p.n) {
-      tplane[isl * p.n + lane] = o.t[k];
-      if constexpr (TRACKED) splane[isl * p.n + lane] = o.s[k];
-      Tplane[isl * p.n + lane] = o.T[k];
+    if (o.live[k] && (NN == 32 || lane < n)) {
+      tplane[base + k * n] = o.t[k];
+      if constexpr (TRACKED) splane[base + k * n] = o.s[k];
+      Tplane[base + k * n] = o.T[k];
     }
   }
 }
@@ -163,13 +168,14 @@ __device__ __forceinline__ void store_octet(const RunParams &p, const Octet<IPW>
 // (last octet only) hold zeros that are never stored or published, so they
 // are stepped too: with no branch per island the islands' Philox chains
 // share one basic block and the scheduler interleaves them.
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
 __device__ __forceinline__ void octet_step(const RunParams &p, Octet<IPW> &o, uint32_t lane,
                                            uint32_t G) {
   const PhiloxHead h = philox_head(p.k0, p.k1, lane, G, kPurposeReplicate);
 #pragma unroll
   for (int k = 0; k < IPW; ++k)
-    counter_step<TRACKED, T2, TWO, FLT>(p, h, lane, o.first + k, G, o.t[k], o.s[k], o.T[k]);
+    counter_step<TRACKED, T2, TWO, FLT, NN>(p, h, lane, o.first + k, G, o.t[k], o.s[k],
+                                            o.T[k]);
 }
 
 // Whether generation G migrates, in 32-bit arithmetic (free-running
@@ -190,12 +196,12 @@ __device__ __forceinline__ uint32_t owned_octets(uint32_t warp, uint32_t nwarps,
 // One generation of one octet: lane 4k + j publishes word j of island k's
 // emigrant record, and lane 4k + d reads the record of island k's neighbour
 // in direction d (`seen`: the newest stamp it has seen from it).
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
 __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> &o,
                                                  uint32_t &seen, uint32_t lane, uint32_t G,
                                                  uint64_t *rec, uint32_t *log,
                                                  uint32_t log_G0, uint32_t log_gens) {
-  const uint32_t n = p.n, first = o.first;
+  const uint32_t n = NN ? (uint32_t)NN : p.n, first = o.first;
   const uint32_t rk = lane >> 2, rd = lane & 3u;
   const bool reader = lane < 4u * IPW && first + rk < p.islands;
   const uint32_t risl = first + rk;
@@ -210,7 +216,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
     uint32_t word = 0, dir = 0;
 #pragma unroll
     for (int k = 0; k < IPW; ++k) {
-      const uint32_t eslot = uindex(__shfl_sync(kFull, m.x, k), n);
+      const uint32_t eslot = uindex_nn<NN>(__shfl_sync(kFull, m.x, k), n);
       const uint32_t dk = __shfl_sync(kFull, m.y, k) >> 30;
       const uint32_t vt = __shfl_sync(kFull, o.t[k], eslot);
       const uint64_t vs = shfl64(o.s[k], eslot);
@@ -254,7 +260,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
       for (uint32_t dd = 0; dd < 4; ++dd) {
         if (bits & (1u << dd)) {
           const uint32_t slot =
-              uindex(__shfl_sync(kFull, pick4(m.x, m.y, m.z, m.w, dd), IPW + k), n);
+              uindex_nn<NN>(__shfl_sync(kFull, pick4(m.x, m.y, m.z, m.w, dd), IPW + k), n);
           const uint32_t src = 4u * k + dd;
           const uint32_t vt = __shfl_sync(kFull, r[0], src);
           const uint64_t vs = shfl64(is, src);
@@ -270,7 +276,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
   } else if (reader && logging) {
     log[((size_t)risl * log_gens + (G - log_G0)) * 4 + rd] = 0;
   }
-  octet_step<TRACKED, T2, TWO, IPW, FLT>(p, o, lane, G);
+  octet_step<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, lane, G);
 }
 
 // Residency bounds (blocks per SM) chosen by measurement at 16.8M agents:
@@ -278,7 +284,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
 constexpr int kAsyncBlocksPerSM = 8;
 constexpr int kBufferedBlocksPerSM = 8;
 
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
 __global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
     step_async_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                       uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
@@ -299,13 +305,13 @@ __global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
       const uint32_t first = (warp + j * nwarps) * IPW;
       const bool reader = lane < 4u * IPW && first + rk < p.islands;
       if (owned > 1 || g == 0) {
-        load_octet<TRACKED>(p, o, first, lane, tplane, splane, Tplane);
+        load_octet<TRACKED, IPW, NN>(p, o, first, lane, tplane, splane, Tplane);
         seen = reader ? seen_io[(first + rk) * 4 + rd] : 0u;
       }
-      async_generation<TRACKED, T2, TWO, IPW, FLT>(p, o, seen, lane, G0 + g, rec, log, log_G0,
-                                                   log_gens);
+      async_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, seen, lane, G0 + g, rec, log,
+                                                       log_G0, log_gens);
       if (owned > 1 || g + 1 == ngen) {
-        store_octet<TRACKED>(p, o, lane, tplane, splane, Tplane);
+        store_octet<TRACKED, IPW, NN>(p, o, lane, tplane, splane, Tplane);
         if (reader) seen_io[(first + rk) * 4 + rd] = seen;
       }
     }
@@ -337,13 +343,13 @@ struct LaneChannel {
   uint32_t posts, taken, waiting;
 };
 
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
 __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IPW> &o,
                                                     LaneChannel &ch, uint32_t lane, uint32_t G,
                                                     bool mig, uint64_t *mail, uint32_t *ack,
                                                     uint4 *inbuf, uint32_t *log,
                                                     uint32_t log_G0, uint32_t log_gens) {
-  const uint32_t n = p.n;
+  const uint32_t n = NN ? (uint32_t)NN : p.n;
   const uint32_t rk = lane >> 2, rd = lane & 3u;
   const uint32_t me = o.first + rk;
   const bool mine = lane < 4u * IPW && me < p.islands;
@@ -401,7 +407,7 @@ __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IP
 #pragma unroll
           for (uint32_t j = 0; j < 4; ++j) {
             const uint32_t slot =
-                uindex(__shfl_sync(kFull, pick4(pv.x, pv.y, pv.z, pv.w, j), src), n);
+                uindex_nn<NN>(__shfl_sync(kFull, pick4(pv.x, pv.y, pv.z, pv.w, j), src), n);
             const uint4 bj = j == 0 ? b0 : j == 1 ? b1 : j == 2 ? b2 : arrived;
             const uint32_t gt = __shfl_sync(kFull, bj.x, src);
             const uint32_t glo = __shfl_sync(kFull, bj.y, src);
@@ -420,7 +426,7 @@ __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IP
     const bool send = (sends >> lane) & 1u;
     if (sends) {
       const Words4 w = philox_rk(p, kSlotEmigrant, me, G, kPurposeMigration);
-      const uint32_t slot = uindex(pick4(w.x, w.y, w.z, w.w, rd), n);
+      const uint32_t slot = uindex_nn<NN>(pick4(w.x, w.y, w.z, w.w, rd), n);
       uint32_t et = 0, eT = 0;
       uint64_t es = 0;
 #pragma unroll
@@ -446,10 +452,10 @@ __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IP
     }
   }
   if (mine && logging) log[((size_t)me * log_gens + (G - log_G0)) * 4 + rd] = entry;
-  octet_step<TRACKED, T2, TWO, IPW, FLT>(p, o, lane, G);
+  octet_step<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, lane, G);
 }
 
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT>
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
 __global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
     step_buffered_kernel(RunParams p, uint32_t G0, uint32_t ngen, uint32_t *__restrict__ tplane,
                          uint64_t *__restrict__ splane, uint32_t *__restrict__ Tplane,
@@ -473,16 +479,16 @@ __global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
       const bool mine = lane < 4u * IPW && first + rk < p.islands;
       const size_t c = 4 * (size_t)(first + rk) + rd;
       if (owned > 1 || g == 0) {
-        load_octet<TRACKED>(p, o, first, lane, tplane, splane, Tplane);
+        load_octet<TRACKED, IPW, NN>(p, o, first, lane, tplane, splane, Tplane);
         if (mine) {
           const uint4 st = chst[c];
           ch = LaneChannel{st.x, st.y, st.z};
         }
       }
-      buffered_generation<TRACKED, T2, TWO, IPW, FLT>(p, o, ch, lane, G0 + g, mig, mail, ack,
-                                                      inbuf, log, log_G0, log_gens);
+      buffered_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, ch, lane, G0 + g, mig, mail,
+                                                          ack, inbuf, log, log_G0, log_gens);
       if (owned > 1 || g + 1 == ngen) {
-        store_octet<TRACKED>(p, o, lane, tplane, splane, Tplane);
+        store_octet<TRACKED, IPW, NN>(p, o, lane, tplane, splane, Tplane);
         if (mine) chst[c] = make_uint4(ch.posts, ch.taken, ch.waiting, 0u);
       }
     }
@@ -497,8 +503,11 @@ constexpr int kBufferedIslandsPerWarp = 4;
 using AsyncFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t *, uint32_t *,
                          uint64_t *, uint32_t *, uint32_t *, uint32_t, uint32_t);
 
-AsyncFn pick_async(bool tracked, bool t2, bool two, bool flt) {
+AsyncFn pick_async(bool tracked, bool t2, bool two, bool flt, bool n32) {
   constexpr int I = kAsyncIslandsPerWarp;
+  if (n32 && tracked && !two && !flt)  // 32-agent islands, the paper's shape
+    return t2 ? step_async_kernel<true, true, false, I, false, 32>
+              : step_async_kernel<true, false, false, I, false, 32>;
   if (flt) {  // general tournament path only
     if (!tracked) return step_async_kernel<false, false, false, I, true>;
     return two ? step_async_kernel<true, false, true, I, true>
@@ -518,8 +527,11 @@ using BufferedFn = void (*)(RunParams, uint32_t, uint32_t, uint32_t *, uint64_t 
                             uint64_t *, uint32_t *, uint4 *, uint4 *, uint32_t *, uint32_t,
                             uint32_t);
 
-BufferedFn pick_buffered(bool tracked, bool t2, bool two, bool flt) {
+BufferedFn pick_buffered(bool tracked, bool t2, bool two, bool flt, bool n32) {
   constexpr int I = kBufferedIslandsPerWarp;
+  if (n32 && tracked && !two && !flt)  // 32-agent islands, the paper's shape
+    return t2 ? step_buffered_kernel<true, true, false, I, false, 32>
+              : step_buffered_kernel<true, false, false, I, false, 32>;
   if (flt) {  // general tournament path only
     if (!tracked) return step_buffered_kernel<false, false, false, I, true>;
     return two ? step_buffered_kernel<true, false, true, I, true>
@@ -579,7 +591,7 @@ constexpr int kFloatIslandsPerWarp = 4;
 // Blocks for a free-running launch: one warp per octet, but never more
 // blocks than the device keeps resident at once, so that every island
 // advances in the same pass over the grid (warps then own several octets).
-uint32_t resident_blocks(const void *fn, uint32_t islands, uint32_t ipw) {
+uint32_t resident_blocks(const void *fn, uint32_t islands, uint32_t ipw, int max_per_sm) {
   const uint32_t wpb = kResidentThreads / 32;
   const uint32_t octets = (islands + ipw - 1) / ipw;
   const uint32_t need = (octets + wpb - 1) / wpb;
@@ -587,6 +599,7 @@ uint32_t resident_blocks(const void *fn, uint32_t islands, uint32_t ipw) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResidentThreads, 0);
+  if (per_sm > max_per_sm) per_sm = max_per_sm;
   const uint32_t cap = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
   return need < cap ? need : cap;
 }
@@ -617,9 +630,10 @@ cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen,
                                  uint64_t *s, uint32_t *T, uint64_t *mail, uint32_t *ack,
                                  uint4 *inbuf, uint4 *chst, uint32_t *log, uint32_t log_G0,
                                  uint32_t log_gens, cudaStream_t stream) {
-  BufferedFn fn =
-      pick_buffered(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
-  const uint32_t blocks = resident_blocks((const void *)fn, p.islands, kBufferedIslandsPerWarp);
+  BufferedFn fn = pick_buffered(p.policy != HSGA_NONE, p.tournament == 2,
+                                p.policy == HSGA_HYBRID, p.flt, p.n == 32);
+  const uint32_t blocks = resident_blocks((const void *)fn, p.islands, kBufferedIslandsPerWarp,
+                                          kBufferedBlocksPerSM);
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, mail, ack, inbuf, chst, log,
                                                log_G0, log_gens);
   return cudaGetLastError();
@@ -629,9 +643,10 @@ cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, ui
                               uint64_t *s, uint32_t *T, uint64_t *rec, uint32_t *seen,
                               uint32_t *log, uint32_t log_G0, uint32_t log_gens,
                               cudaStream_t stream) {
-  AsyncFn fn =
-      pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID, p.flt);
-  const uint32_t blocks = resident_blocks((const void *)fn, p.islands, kAsyncIslandsPerWarp);
+  AsyncFn fn = pick_async(p.policy != HSGA_NONE, p.tournament == 2, p.policy == HSGA_HYBRID,
+                          p.flt, p.n == 32);
+  const uint32_t blocks = resident_blocks((const void *)fn, p.islands, kAsyncIslandsPerWarp,
+                                          kAsyncBlocksPerSM);
   fn<<<blocks, kResidentThreads, 0, stream>>>(p, G0, ngen, t, s, T, rec, seen, log, log_G0,
                                                log_gens);
   return cudaGetLastError();

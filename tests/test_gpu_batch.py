@@ -99,3 +99,40 @@ def test_batch_sample_and_progress_queries(hb, orc):
 def test_footprint_is_host_only(hb):
     cfg = hb.make_config(rows=64, cols=64, n=32)
     assert hb.hsga_run_footprint(cfg) >= 64 * 64 * 32 * 24
+
+
+def runs_of_32(seed, count):
+    """32-agent runs (the paper's island size) of every configuration the
+    batch supports, on grids whose island count is and is not a multiple of
+    the six-island work item."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        rows, cols = [(2, 3), (3, 4), (4, 6), (5, 7), (6, 6), (1, 13), (8, 9)][i % 7]
+        out.append((int(rng.integers(30, 250)),
+                    dict(rows=rows, cols=cols, n=32, tournament=int(rng.choice([1, 2, 2, 3, 5])),
+                         policy=str(rng.choice(["steady", "tilted", "stretched", "trivial",
+                                                "none", "hybrid"])),
+                         bits=int(rng.choice([1, 2, 4])), p_ben=float(rng.choice([0.0, 0.05])),
+                         p_del=float(rng.choice([0.0, 0.03])),
+                         interval=int(rng.choice([1, 1, 2, 0])),
+                         coarsen=int(rng.choice([1, 1, 2])), seed=int(rng.integers(1, 2**40)))))
+    return out
+
+
+def test_batch_of_32_agent_runs_equals_oracle(hb, orc, oracle_pool):
+    runs = runs_of_32(7, 21)
+    want = [oracle_pool.submit(orc.run, oracle_config(orc, kw), None, None, 0, gens)
+            for gens, kw in runs]
+    with hb.Batch() as b:
+        ids = [b.add(gens, **kw) for gens, kw in runs[:12]]
+        b.run(17)                                          # an odd tick count: parity moves
+        ids += [b.add(gens, **kw) for gens, kw in runs[12:]]
+        b.run(10**6)
+        b.sync()
+        for rid, (gens, kw), fut in zip(ids, runs, want):
+            assert b.info(rid)["generation"] == gens
+            t, s = b.population(rid)
+            ot, os_, _ = fut.result()
+            assert np.array_equal(t, ot), (rid, kw)
+            assert np.array_equal(s, os_), (rid, kw)
