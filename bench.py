@@ -67,6 +67,7 @@ KERNEL_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",
                   "paper_2404_10861_gb300/csrc/hsga_island.cuh",
                   "paper_2404_10861_gb300/csrc/hsga_internal.h",
                   "paper_2404_10861_gb300/csrc/hsga_kernels.cu",
+                  "paper_2404_10861_gb300/csrc/hsga_stage.cuh",
                   "paper_2404_10861_gb300/csrc/hsga_staged.cu"]
 PROFILE = os.path.join(ROOT, "profiles", "step_streamed_wafer.md")
 FREE_RUNNING_SOURCES = ["paper_2404_10861_gb300/csrc/hsga_device.cuh",

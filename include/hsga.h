@@ -58,7 +58,11 @@ typedef enum hsga_status {
   HSGA_ERR_CUDA = -3,         /* a CUDA runtime call failed */
   HSGA_ERR_DEVICE = -4,       /* a kernel reported an inconsistent state */
   HSGA_ERR_WAIT_TIMEOUT = -5, /* a bounded device-side wait ran out */
-  HSGA_ERR_UNSUPPORTED = -6   /* valid request the library does not support */
+  HSGA_ERR_UNSUPPORTED = -6,  /* valid request the library does not support */
+  HSGA_ERR_NOT_CAPTURABLE = -7 /* a call that waits for its stream, made while that
+                                  stream is being captured into a CUDA graph; the
+                                  call returns before touching the stream, so the
+                                  capture stays valid */
 } hsga_status;
 
 /* Surface curation policies.  The paper defines steady (retained time points

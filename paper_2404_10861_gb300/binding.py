@@ -24,7 +24,8 @@ KERNEL_AUTO, KERNEL_STREAMED, KERNEL_RESIDENT, KERNEL_RESIDENT_GRID = 0, 1, 2, 3
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed",
           -3: "CUDA runtime error", -4: "kernel reported an inconsistent state",
-          -5: "bounded device wait timed out", -6: "unsupported"}
+          -5: "bounded device wait timed out", -6: "unsupported",
+          -7: "call waits for a stream under graph capture"}
 
 
 class HsgaError(RuntimeError):

@@ -453,6 +453,7 @@ int hsga_batch_add(hsga_batch *b, const hsga_config *cfg, uint64_t generations,
 
 int hsga_batch_run(hsga_batch *b, uint64_t ticks) {
   if (!b) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(b->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   cudaError_t e = upload_runs(b);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? HSGA_ERR_OOM : HSGA_ERR_CUDA;
   uint64_t left = ticks;
@@ -497,6 +498,7 @@ int hsga_batch_info(const hsga_batch *b, uint32_t run, hsga_batch_run_info *out)
 
 int hsga_batch_get_population(hsga_batch *b, uint32_t run, uint32_t *trait, uint64_t *surf) {
   if (!b || !trait || run >= b->runs.size() || !b->runs[run].live) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(b->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   const HostRun &R = b->runs[run];
   const int par = (int)((R.start_tick + run_generation(b, R)) & 1);
   cudaError_t e = cudaMemcpyAsync(trait, R.trait[par], sizeof(uint32_t) * R.agents,
@@ -515,6 +517,7 @@ int hsga_batch_sample(hsga_batch *b, uint32_t run, uint32_t k, uint32_t *out_wor
   const HostRun &R = b->runs[run];
   if (k > R.p.islands) return HSGA_ERR_INVALID_ARG;
   if (k == 0) return HSGA_OK;
+  if (stream_capturing(b->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   const uint64_t G = run_generation(b, R);
   const int par = (int)((R.start_tick + G) & 1);
   const size_t scratch_bytes = sample_scratch_bytes(R.p, k);
@@ -577,6 +580,7 @@ int hsga_run_footprint(const hsga_config *cfg, uint64_t *bytes) {
 
 int hsga_batch_synchronize(hsga_batch *b) {
   if (!b) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(b->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? HSGA_OK : HSGA_ERR_CUDA;
 }
 

@@ -286,6 +286,7 @@ const char *hsga_status_string(int s) {
     case HSGA_ERR_DEVICE: return "kernel reported an inconsistent state";
     case HSGA_ERR_WAIT_TIMEOUT: return "bounded device wait timed out";
     case HSGA_ERR_UNSUPPORTED: return "unsupported";
+    case HSGA_ERR_NOT_CAPTURABLE: return "call waits for a stream under graph capture";
     default: return "unknown status";
   }
 }
@@ -381,6 +382,8 @@ int hsga_set_population(hsga_grid *g, const uint32_t *trait, const uint64_t *sur
   if (!g || !trait || generation > kMaxGeneration) return HSGA_ERR_INVALID_ARG;
   const bool tracked = g->surf[0] != nullptr;
   if (tracked && !surf) return HSGA_ERR_INVALID_ARG;
+  if ((!is_device_ptr(trait) || (tracked && !is_device_ptr(surf))) && stream_capturing(g->stream))
+    return HSGA_ERR_NOT_CAPTURABLE;
   g->cur = 0;
   cudaError_t e = copy_in(g->trait[0], trait, sizeof(uint32_t) * g->agents, g->stream);
   if (e == cudaSuccess && tracked)
@@ -400,6 +403,8 @@ int hsga_set_population(hsga_grid *g, const uint32_t *trait, const uint64_t *sur
 int hsga_get_population(hsga_grid *g, uint32_t *trait, uint64_t *surf) {
   if (!g || !trait) return HSGA_ERR_INVALID_ARG;
   const bool tracked = g->surf[0] != nullptr;
+  if ((!is_device_ptr(trait) || (surf && !is_device_ptr(surf))) && stream_capturing(g->stream))
+    return HSGA_ERR_NOT_CAPTURABLE;
   cudaError_t e = cudaMemcpyAsync(trait, g->trait[g->cur], sizeof(uint32_t) * g->agents,
                                   cudaMemcpyDefault, g->stream);
   if (e == cudaSuccess && surf) {
@@ -585,6 +590,7 @@ int hsga_set_fossil_sampling(hsga_grid *g, uint64_t every, uint32_t k, uint32_t 
 int hsga_get_fossils(hsga_grid *g, uint32_t *out_words, uint32_t *out_island_slot,
                      uint32_t max_records, uint32_t *count) {
   if (!g || !count) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   *count = g->fossil_count;
   const uint32_t m = g->fossil_count < max_records ? g->fossil_count : max_records;
   if (m == 0) return HSGA_OK;
@@ -602,6 +608,7 @@ int hsga_get_counters(hsga_grid *g, uint32_t *T_out) {
   if (!g || !T_out) return HSGA_ERR_INVALID_ARG;
   cudaError_t e;
   const bool dev = is_device_ptr(T_out);
+  if (!dev && stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   if (g->async) {
     e = cudaMemcpyAsync(T_out, g->tcount, sizeof(uint32_t) * g->agents, cudaMemcpyDefault,
                         g->stream);
@@ -640,6 +647,7 @@ int hsga_set_async_log(hsga_grid *g, uint32_t generations) {
 int hsga_get_async_log(hsga_grid *g, uint32_t *out) {
   if (!g || !out) return HSGA_ERR_INVALID_ARG;
   if (!g->alog) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   cudaError_t e = cudaMemcpyAsync(out, g->alog,
                                   sizeof(uint32_t) * 4 * (size_t)g->p.islands * g->alog_gens,
                                   cudaMemcpyDefault, g->stream);
@@ -650,6 +658,7 @@ int hsga_get_async_log(hsga_grid *g, uint32_t *out) {
 int hsga_get_migration_buffers(hsga_grid *g, uint32_t *chan_out, uint32_t *inbuf_out) {
   if (!g || !chan_out) return HSGA_ERR_INVALID_ARG;
   if (!g->buffered) return HSGA_ERR_UNSUPPORTED;
+  if (stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   const size_t C = 4 * (size_t)g->p.islands;
   // {posts, taken, waiting, 0} per channel -> 3 words per channel
   cudaError_t e = cudaMemcpy2DAsync(chan_out, 3 * sizeof(uint32_t), g->chst, sizeof(uint4),
@@ -685,6 +694,7 @@ int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
   if (!g || (k > 0 && !out_words)) return HSGA_ERR_INVALID_ARG;
   if (k > g->p.islands) return HSGA_ERR_INVALID_ARG;
   if (k == 0) return HSGA_OK;
+  if (stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   const int sr = ensure_sample_scratch(g, k);
   if (sr != HSGA_OK) return sr;
   if (g->wide) {
@@ -741,6 +751,7 @@ int hsga_sample_surfaces(hsga_grid *g, uint32_t k, uint32_t *out_words,
 
 int hsga_synchronize(hsga_grid *g) {
   if (!g) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return HSGA_ERR_CUDA;
   e = cudaGetLastError();
@@ -769,6 +780,7 @@ int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
 // Checkpoint layout: magic, config, G, then traits and surfaces.
 int hsga_save(hsga_grid *g, void *buf, size_t *len) {
   if (!g || !len) return HSGA_ERR_INVALID_ARG;
+  if (buf && stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   if (g->async) return HSGA_ERR_UNSUPPORTED;
   const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 4 + g->swords * 8;
   if (!buf) {
@@ -794,6 +806,7 @@ int hsga_save(hsga_grid *g, void *buf, size_t *len) {
 
 int hsga_load(hsga_grid *g, const void *buf, size_t len) {
   if (!g || !buf) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing(g->stream)) return HSGA_ERR_NOT_CAPTURABLE;
   if (g->async) return HSGA_ERR_UNSUPPORTED;
   const size_t need = sizeof(uint64_t) * 2 + sizeof(hsga_config) + g->agents * 4 + g->swords * 8;
   if (len < need) return HSGA_ERR_INVALID_ARG;
@@ -912,6 +925,7 @@ int hsga_wait_probe(const uint64_t *record_dev, uint32_t seq, uint64_t limit_ns,
   if (!record_dev || limit_ns > 1000000000ull || !is_device_ptr(record_dev) ||
       ((uintptr_t)record_dev % 8) != 0)
     return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing((cudaStream_t)cuda_stream)) return HSGA_ERR_NOT_CAPTURABLE;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   AllocHooks al = current_allocator();
   void *scratch = device_alloc(al, 32, st);  // error word + two results
@@ -978,4 +992,12 @@ void device_free(const AllocHooks &h, void *ptr, cudaStream_t s) {
   dev_free(Allocator{h.alloc, h.free_fn, h.ctx}, ptr, s);
 }
 bool device_pointer(const void *ptr) { return is_device_ptr(ptr); }
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
 }  // namespace hsga

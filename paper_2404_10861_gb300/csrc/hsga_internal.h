@@ -101,6 +101,10 @@ void *device_alloc(const AllocHooks &h, size_t bytes, cudaStream_t s);
 void device_free(const AllocHooks &h, void *ptr, cudaStream_t s);
 bool device_pointer(const void *ptr);
 
+// Whether `s` is being captured into a CUDA graph (calls that wait for their
+// stream return HSGA_ERR_NOT_CAPTURABLE then; defined in hsga_capi.cu).
+bool stream_capturing(cudaStream_t s);
+
 // Configuration checks and kernel parameters (defined in hsga_capi.cu).
 int validate_config(const hsga_config *c);
 RunParams params_from_config(const hsga_config *c);

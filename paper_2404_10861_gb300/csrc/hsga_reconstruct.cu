@@ -338,6 +338,7 @@ int hsga_reconstruct(const uint64_t *surf, uint32_t k, uint32_t surface_words, u
   if (policy > HSGA_HYBRID || policy == HSGA_NONE) return HSGA_ERR_INVALID_ARG;
   const uint64_t need_nodes = 2ull * k + 1;
   if (capacity < need_nodes) return HSGA_ERR_INVALID_ARG;
+  if (stream_capturing((cudaStream_t)cuda_stream)) return HSGA_ERR_NOT_CAPTURABLE;
   // retained deposition times in ascending order (the same for every sample)
   const uint32_t S = 64 * K / b;
   const uint64_t kk = deposit_interval > 1 ? deposit_interval : 1;

@@ -52,3 +52,41 @@ def test_probe_argument_checks(hb):
         hb.hsga_wait_probe(record, 1, 2_000_000_000)        # over the 1 s cap
     with pytest.raises(hb.HsgaError):
         hb.hsga_wait_probe(np.zeros(4, np.uint64), 1, 1000)  # host memory
+
+
+def test_synchronous_calls_refuse_a_capturing_stream(hb, orc):
+    """Calls that must wait for their stream return HSGA_ERR_NOT_CAPTURABLE
+    when that stream is being captured into a CUDA graph, before touching it,
+    so the capture stays valid and the grid keeps working afterwards."""
+    import ctypes
+    import torch
+    NOT_CAPTURABLE = -7
+    stream = torch.cuda.Stream()
+    kw = dict(rows=8, cols=8, n=32, tournament=2, policy="tilted", bits=1, p_ben=1e-3, seed=3)
+    c = orc.Config(rows=8, cols=8, n=32, tournament=2, policy=orc.TILTED, bits=1, W=2,
+                   interval=1, p_ben=1e-3, seed=3)
+    with hb.Grid(stream=stream.cuda_stream, **kw) as g:
+        g.run(20)
+        g.sync()
+        words = np.zeros((4, 4), dtype=np.uint32)
+        where = np.zeros((4, 2), dtype=np.uint32)
+        t = np.zeros(c.agents, dtype=np.uint32)
+        s = np.zeros(c.agents, dtype=np.uint64)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            graph.capture_begin(capture_error_mode="thread_local")
+            try:
+                st_sync = hb.lib().hsga_synchronize(g.handle)
+                st_sample = hb.lib().hsga_sample_surfaces(
+                    g.handle, 4, ctypes.c_void_p(words.ctypes.data),
+                    ctypes.c_void_p(where.ctypes.data))
+                st_get = hb.lib().hsga_get_population(
+                    g.handle, ctypes.c_void_p(t.ctypes.data), ctypes.c_void_p(s.ctypes.data))
+            finally:
+                graph.capture_end()
+        assert (st_sync, st_sample, st_get) == (NOT_CAPTURABLE,) * 3
+        g.run(15)
+        g.sync()
+        got = g.population()
+    want = orc.run(c, generations=35)[:2]
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
