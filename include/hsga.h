@@ -283,6 +283,20 @@ int hsga_set_async_log(hsga_grid *g, uint32_t generations);
  * Synchronous. */
 int hsga_get_async_log(hsga_grid *g, uint32_t *out);
 
+/* Free-running grids: generations (1..65536) by which a warp advances each
+ * island octet (four consecutive islands) it owns before it moves to its
+ * next one; the octet's genomes stay in registers meanwhile, so a grid too
+ * large to stay on chip streams through device memory once per `generations`
+ * generations instead of every generation.  At any moment the islands being
+ * advanced form a band of consecutive islands; migrants from neighbours
+ * outside the band are the latest those neighbours published, as free-
+ * running migration allows ("Methods › Asynchronous Island-model Genetic
+ * Algorithm": islands run without a global clock), and logged runs replay
+ * exactly.  1 (the default) advances every octet one generation at a time,
+ * the whole grid together.  HSGA_ERR_UNSUPPORTED for synchronous grids.
+ * Host function; applies to later hsga_run_generations calls. */
+int hsga_set_octet_slice(hsga_grid *g, uint32_t generations);
+
 /* BUFFERED grids: channel state.  chan_out (islands * 4 * 3 uint32) receives
  * per island and direction {posts sent toward d, number of the last post
  * taken from d, genomes waiting in the receive buffer of d}; inbuf_out (may be

@@ -131,6 +131,7 @@ _SIGS = {
                            ctypes.c_int),
     "hsga_batch_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "hsga_batch_destroy": ([ctypes.c_void_p], None),
+    "hsga_set_octet_slice": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "hsga_philox_throughput": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                 ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
                                 ctypes.c_void_p], ctypes.c_int),
@@ -334,6 +335,11 @@ def hsga_philox_device(seed: int, c0: int, count: int, c1: int, c2: int, c3: int
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(lib().hsga_philox_device(seed, c0, count, c1, c2, c3, _ptr(out_dev), s),
            "hsga_philox_device")
+
+
+def hsga_set_octet_slice(g, generations: int):
+    """Free-running grids: generations per visit of each island octet."""
+    _check(lib().hsga_set_octet_slice(g, int(generations)), "hsga_set_octet_slice")
 
 
 def hsga_philox_throughput(seed: int, threads: int, blocks_per_thread: int, c2: int, c3: int,

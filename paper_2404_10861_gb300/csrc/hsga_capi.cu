@@ -65,6 +65,7 @@ struct hsga_grid {
   uint4 *chst = nullptr;
   uint32_t *alog = nullptr;
   uint32_t alog_gens = 0;
+  uint32_t octet_slice = 1;  // free-running: generations per octet visit
   uint64_t alog_G0 = 0;
   uint64_t G = 0;
   bool premigrated = false;
@@ -484,7 +485,7 @@ int advance(hsga_grid *g, uint64_t n) {
     const uint64_t slice = 1u << 16;
     for (uint64_t done = 0; done < n && e == cudaSuccess;) {
       const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
-      e = launch_step_buffered(g->p, (uint32_t)(g->G + done), m, g->trait[g->cur],
+      e = launch_step_buffered(g->p, (uint32_t)(g->G + done), m, g->octet_slice, g->trait[g->cur],
                                g->surf[g->cur], g->tcount, g->mail, g->ack, g->inbuf, g->chst,
                                g->alog, (uint32_t)g->alog_G0, g->alog_gens, g->stream);
       g->launches++;
@@ -494,7 +495,8 @@ int advance(hsga_grid *g, uint64_t n) {
     const uint64_t slice = 1u << 16;
     for (uint64_t done = 0; done < n && e == cudaSuccess;) {
       const uint32_t m = (uint32_t)((n - done) < slice ? (n - done) : slice);
-      e = launch_step_async(g->p, (uint32_t)(g->G + done), m, g->trait[g->cur], g->surf[g->cur],
+      e = launch_step_async(g->p, (uint32_t)(g->G + done), m, g->octet_slice, g->trait[g->cur],
+                            g->surf[g->cur],
                             g->tcount, reinterpret_cast<uint64_t *>(g->rec), g->seen, g->alog,
                             (uint32_t)g->alog_G0, g->alog_gens, g->stream);
       g->launches++;
@@ -642,6 +644,14 @@ int hsga_set_async_log(hsga_grid *g, uint32_t generations) {
   g->alog_gens = generations;
   g->alog_G0 = g->G;
   return cuda_status(e);
+}
+
+int hsga_set_octet_slice(hsga_grid *g, uint32_t generations) {
+  if (!g) return HSGA_ERR_INVALID_ARG;
+  if (!g->async) return HSGA_ERR_UNSUPPORTED;
+  if (generations == 0 || generations > (1u << 16)) return HSGA_ERR_INVALID_ARG;
+  g->octet_slice = generations;
+  return HSGA_OK;
 }
 
 int hsga_get_async_log(hsga_grid *g, uint32_t *out) {

@@ -81,13 +81,16 @@ cudaError_t launch_gather_wide(const RunParams &p, uint32_t G, uint32_t k, const
 cudaError_t launch_step_float(const RunParams &p, uint32_t G, const uint32_t *tin,
                               const uint64_t *sin, uint32_t *tout, uint64_t *sout,
                               cudaStream_t stream);
-cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t *t,
-                                 uint64_t *s, uint32_t *T, uint64_t *mail, uint32_t *ack,
-                                 uint4 *inbuf, uint4 *chst, uint32_t *log, uint32_t log_G0,
-                                 uint32_t log_gens, cudaStream_t stream);
-cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t *t,
-                              uint64_t *s, uint32_t *T, uint64_t *rec, uint32_t *seen,
-                              uint32_t *log, uint32_t log_G0, uint32_t log_gens,
+// Free-running generations (hsga_async.cu).  slice: generations each warp
+// advances an island octet by per visit (1: the whole grid one generation at
+// a time).
+cudaError_t launch_step_buffered(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t slice,
+                                 uint32_t *t, uint64_t *s, uint32_t *T, uint64_t *mail,
+                                 uint32_t *ack, uint4 *inbuf, uint4 *chst, uint32_t *log,
+                                 uint32_t log_G0, uint32_t log_gens, cudaStream_t stream);
+cudaError_t launch_step_async(const RunParams &p, uint32_t G0, uint32_t ngen, uint32_t slice,
+                              uint32_t *t, uint64_t *s, uint32_t *T, uint64_t *rec,
+                              uint32_t *seen, uint32_t *log, uint32_t log_G0, uint32_t log_gens,
                               cudaStream_t stream);
 
 // Device memory through the registered allocator hooks (hsga_capi.cu).

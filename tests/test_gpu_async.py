@@ -120,3 +120,47 @@ def test_async_replicates_replay_exactly(hb, orc):
     print(f"free-running takes per island-generation {rate:.3f}; mean trait "
           f"{gpu[:, 0].mean():.2f} vs synchronous {sync[:, 0].mean():.2f}; mean pairwise "
           f"distance {gpu[:, 1].mean():.1f} vs {sync[:, 1].mean():.1f}")
+
+
+@pytest.mark.parametrize("mode", ["async", "buffered"])
+@pytest.mark.parametrize("slice_", [1, 7])
+def test_octet_slices_replay_exactly(hb, orc, mode, slice_):
+    """Octets advanced several generations per visit (hsga_set_octet_slice)
+    on a grid with more octets than resident warps, so warps page octets in
+    and out: the logged run still replays exactly (latest-emigrant records
+    with the oracle's async replay, per-neighbour buffers with its buffered
+    replay)."""
+    kw = dict(rows=192, cols=160, n=32, tournament=2, policy="tilted", bits=1, p_ben=0.02,
+              seed=31)
+    c = ocfg(orc, kw)
+    trait, surf = inputs.small_trait_population(c.agents, seed=5, levels=4)
+    G0, gens = 50, 30
+    with hb.Grid(mode=mode, **kw) as g:
+        g.set_population(trait, surf, G0)
+        hb.hsga_set_octet_slice(g.handle, slice_)
+        hb.hsga_set_async_log(g.handle, gens)
+        g.run(13)
+        g.run(gens - 13)
+        g.sync()
+        t, s = g.population()
+        T = g.counters()
+        log = hb.hsga_get_async_log(g.handle, c.islands, gens)
+    T0 = np.full(c.agents, G0, np.uint32)
+    if mode == "async":
+        sched = np.where(log > 0, log - np.uint32(G0), 0).astype(np.uint32)
+        ot, os_, oT = orc.run_async(c, trait, surf, T0, G0, gens, sched)
+        assert (sched > 0).sum() > 0
+    else:
+        ot, os_, oT, _, _ = orc.run_buffered(c, trait, surf, T0, G0, gens, log)
+        assert (log >> 1).sum() > 0
+    assert np.array_equal(t, ot) and np.array_equal(s, os_) and np.array_equal(T, oT)
+
+
+def test_octet_slice_is_only_for_free_running_grids(hb):
+    with hb.Grid(rows=4, cols=4, n=32) as g:
+        with pytest.raises(hb.HsgaError):
+            hb.hsga_set_octet_slice(g.handle, 4)
+    with hb.Grid(rows=4, cols=4, n=32, mode="async") as g:
+        for bad in (0, 65537):
+            with pytest.raises(hb.HsgaError):
+                hb.hsga_set_octet_slice(g.handle, bad)
