@@ -178,10 +178,11 @@ __device__ __forceinline__ void octet_step(const RunParams &p, Octet<IPW> &o, ui
                                             o.T[k]);
 }
 
-// Whether generation G migrates, in 32-bit arithmetic (free-running
-// generations stay below 2^32).  The buffered kernel evaluates it once per
-// generation per warp (208 -> 203 us per generation at 16.8M agents); the
-// latest-emigrant kernel measured slightly faster with the test per octet.
+// Whether generation G migrates, in 32-bit arithmetic with the every-
+// generation case first (free-running generations stay below 2^32).  The
+// buffered kernel evaluates it once per generation per warp (208 -> 203 us
+// per generation at 16.8M agents, against a 64-bit modulo in every octet's
+// generation); the latest-emigrant kernel per octet.
 __device__ __forceinline__ bool migrates32(const RunParams &p, uint32_t G) {
   return p.interval == 1u || (p.interval != 0u && G % p.interval == 0u);
 }
@@ -206,7 +207,7 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
   const bool reader = lane < 4u * IPW && first + rk < p.islands;
   const uint32_t risl = first + rk;
   const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
-  if (migrates(p, G)) {
+  if (migrates32(p, G)) {
     // block lane b: b < IPW the emigrant block of island b, IPW <= b < 2 IPW
     // the placement block of island b - IPW
     const uint32_t bk = lane < (uint32_t)IPW ? lane : (lane < 2u * IPW ? lane - IPW : 0u);

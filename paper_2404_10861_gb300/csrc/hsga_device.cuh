@@ -355,12 +355,13 @@ __device__ __forceinline__ uint32_t level_site32(bool tilted, uint32_t t1, uint3
                                                  uint32_t S) {
   const uint32_t h = (uint32_t)__ffs((int)t1) - 1u;  // t1 > 0
   uint32_t level, j;
+  // t1 >> k for k up to 63 (0 from 32 on): a clamped funnel shift
   if (h + 1u < L) {
     level = h;
-    j = (uint32_t)((uint64_t)t1 >> (h + 1u));
+    j = __funnelshift_rc(t1, 0u, h + 1u);
   } else {
     level = L - 1u;
-    j = (uint32_t)((uint64_t)t1 >> (L - 1u)) - 1u;
+    j = __funnelshift_rc(t1, 0u, L - 1u) - 1u;
   }
   if (tilted) return level * W + (j & (W - 1u));
   return j < W ? level * W + j : S;
@@ -375,8 +376,15 @@ __device__ __forceinline__ uint32_t site_of32(const RunParams &p, uint32_t T) {
 // Writes the b-bit differentia v into site `site` (< S) of a 64-bit surface.
 __device__ __forceinline__ uint64_t put_site(uint64_t s, uint32_t site, uint32_t bits,
                                              uint64_t vmask, uint32_t v) {
+  // b divides 32, so the field lies within one 32-bit half of the surface
   const uint32_t at = site * bits;
-  return (s & ~(vmask << at)) | (((uint64_t)v & vmask) << at);
+  const uint32_t sh = at & 31u;
+  const uint32_t m = (uint32_t)vmask << sh;
+  const uint32_t val = (v << sh) & m;
+  uint32_t lo = (uint32_t)s, hi = (uint32_t)(s >> 32);
+  if (at & 32u) hi = (hi & ~m) | val;
+  else lo = (lo & ~m) | val;
+  return ((uint64_t)hi << 32) | lo;
 }
 
 // a6 for one genome with its own counter T: the site(s) of deposition T
