@@ -1,9 +1,11 @@
 """Multi-rank decomposition of the island grid, on CPU ranks (gloo, world
-size 2): the torus split into row bands, each rank advancing its band with
-the oracle's step functions and exchanging only the emigrant records of its
-first and last rows with the neighbouring bands every generation, must equal
-the single-domain run bit-exactly.  This is the exchange a multi-GPU run
-would perform (one 16-byte record per boundary island per generation).
+sizes 2 and 3): the torus split into row bands, each rank advancing its band
+with the oracle's step functions and exchanging only the emigrant records of
+its first and last rows with the two neighbouring bands every generation
+(point-to-point sends and receives, no collective), must equal the
+single-domain run bit-exactly.  This is the exchange a multi-GPU run would
+perform (one 16-byte record per boundary island per generation, to the band
+above and the band below).
 """
 import os
 import socket
@@ -55,18 +57,22 @@ def worker(rank, world, port, kw, G, out_path):
     active[:B * C] = 1
     trait = np.zeros(L * n, dtype=np.uint32)
     surf = np.zeros(L * n, dtype=np.uint64)
+    up, down = (rank - 1) % world, (rank + 1) % world   # owners of rows top and bot
+    FIRST, LAST = 1, 2                                   # message tags: which row is sent
     for G_ in range(G):
         rec = oracle.emigrate(cfg, band_gid, trait[:B * C * n], surf[:B * C * n], G_)
-        # exchange first / last row records with every rank, pick the halos
-        mine = torch.from_numpy(np.concatenate([rec[:C], rec[-C:]]).astype(np.int64))
-        allrows = [torch.zeros_like(mine) for _ in range(world)]
-        dist.all_gather(allrows, mine)
-        owner = {}
-        for q in range(world):
-            q0, q1 = band_rows(R, world, q)
-            owner[q0] = allrows[q][:C].numpy().astype(np.uint32)
-            owner[q1 - 1] = allrows[q][C:].numpy().astype(np.uint32)
-        rec_local = np.concatenate([rec, owner[top], owner[bot]])
+        # my first row is the bottom halo of the band above, my last row the
+        # top halo of the band below; receive theirs in turn
+        first = torch.from_numpy(rec[:C].astype(np.int64))
+        last = torch.from_numpy(rec[-C:].astype(np.int64))
+        top_halo = torch.zeros_like(first)
+        bot_halo = torch.zeros_like(last)
+        reqs = [dist.isend(first, up, tag=FIRST), dist.isend(last, down, tag=LAST),
+                dist.irecv(top_halo, up, tag=LAST), dist.irecv(bot_halo, down, tag=FIRST)]
+        for q in reqs:
+            q.wait()
+        rec_local = np.concatenate([rec, top_halo.numpy().astype(np.uint32),
+                                    bot_halo.numpy().astype(np.uint32)])
         t2, s2 = oracle.immigrate_select(cfg, gid, nbr.reshape(-1), active, trait, surf,
                                          rec_local, G_)
         trait[:B * C * n] = t2[:B * C * n]
@@ -76,11 +82,11 @@ def worker(rank, world, port, kw, G, out_path):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("rows,cols,G", [(6, 5, 40), (5, 4, 25), (3, 7, 30)])
-def test_row_bands_equal_single_domain(orc, tmp_path, rows, cols, G):
+@pytest.mark.parametrize("world,rows,cols,G", [(2, 6, 5, 40), (2, 5, 4, 25), (2, 3, 7, 30),
+                                               (3, 7, 4, 30), (3, 3, 5, 20)])
+def test_row_bands_equal_single_domain(orc, tmp_path, world, rows, cols, G):
     kw = dict(rows=rows, cols=cols, n=8, tournament=2, policy=orc.TILTED, bits=2, W=2,
               interval=1, p_ben=0.02, p_del=0.01, seed=31)
-    world = 2
     out = str(tmp_path / "band")
     mp.start_processes(worker, args=(world, free_port(), kw, G, out), nprocs=world,
                        join=True, start_method="spawn")
