@@ -776,7 +776,7 @@ int hsga_get_stats(const hsga_grid *g, hsga_stats *out) {
   out->replications = g->replications;
   out->kernel_launches = g->launches;
   out->kernel = !g->resident ? HSGA_KERNEL_STREAMED
-                : (g->plan.block_sync ? HSGA_KERNEL_RESIDENT : HSGA_KERNEL_RESIDENT_GRID);
+                : (g->plan.mode == kBlockSync ? HSGA_KERNEL_RESIDENT : HSGA_KERNEL_RESIDENT_GRID);
   if (g->resident) {
     out->islands_per_warp = (uint32_t)g->plan.ipw;
     out->warps_per_block = (uint32_t)g->plan.warps_per_block;

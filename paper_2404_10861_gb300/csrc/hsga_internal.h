@@ -22,12 +22,20 @@ constexpr int kResidentThreads = 128;   // resident kernel block: 4 warps
 constexpr uint32_t kSampleSmemMax = 12288;  // largest k sampled by the shared-memory kernel
 constexpr uint64_t kWaitNs = 1000000000ull; // bounded device wait: 1 s
 
+// How the resident kernel exchanges emigrant records: polled stamped records
+// in global memory; the whole grid in one block (shared memory, block
+// barriers); or tiles of islands per block (shared memory inside a tile,
+// polled records across tiles).
+enum ResidentMode { kPolled = 0, kBlockSync = 1, kTiled = 2 };
+constexpr bool kResidentTiles = true;   // multi-block grids use kTiled when a tile shape fits
+
 struct ResidentPlan {
   int ap = 0;      // agents per lane (1: n <= 32, 2: n <= 64)
   int ipw = 0;     // islands per warp
   int blocks = 0;  // cooperative grid
   int warps_per_block = kResidentThreads / 32;
-  bool block_sync = false;  // whole grid in one block: shared-memory records, block barriers
+  int mode = kPolled;
+  uint32_t tile = 0;  // kTiled: log2(tile rows) | log2(tile columns) << 8
 };
 
 // err: the grid's device error word (bounded waits report timeouts there).

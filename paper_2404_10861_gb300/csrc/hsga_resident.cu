@@ -92,24 +92,59 @@ __global__ void wait_probe_kernel(const uint64_t *record, uint32_t seq, uint64_t
   out[1] = global_ns() - t0;
 }
 
-// BLOCKSYNC: the whole grid lives in one thread block (at most 32 warps);
-// records go to shared memory and one __syncthreads per migration replaces
-// the record polling (the record buffer of migration m is rewritten at m+2, after the
-// barrier of m+1, which every reader of m has passed).
-template <int AP, int IPW, bool TRACKED, bool BLOCKSYNC>
-__global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
+// Three ways of exchanging the emigrant records (MODE):
+//  kPolled:    every island polls its four neighbours' records in global
+//              memory (warps numbered in row-major island order).
+//  kBlockSync: the whole grid lives in one thread block (at most 32 warps);
+//              records go to shared memory and one __syncthreads per
+//              migration replaces the polling (the record buffer of
+//              migration m is rewritten at m+2, after the barrier of m+1,
+//              which every reader of m has passed).
+//  kTiled:     each block holds a 2^ltr x 2^ltc tile of islands, one per
+//              warp; neighbours inside the tile are read from shared memory
+//              after one block barrier per migration, and only neighbours in
+//              other tiles are polled in global memory (islands on the tile's
+//              edge publish there as well).  The barrier also spreads a
+//              failed wait to the whole block, so that every warp leaves at
+//              the same barrier.
+template <int AP, int IPW, bool TRACKED, int MODE>
+__global__ void __launch_bounds__(MODE == kPolled ? kResidentThreads : 1024)
     step_resident_kernel(RunParams p, uint32_t G0, uint32_t ngen, int premigrated,
-                         uint32_t *__restrict__ tplane, uint64_t *__restrict__ splane,
-                         uint64_t *__restrict__ rec, int *__restrict__ err) {
-  __shared__ uint4 srec[BLOCKSYNC ? 2 * 32 * IPW : 1];
+                         uint32_t tile, uint32_t *__restrict__ tplane,
+                         uint64_t *__restrict__ splane, uint64_t *__restrict__ rec,
+                         int *__restrict__ err) {
+  constexpr bool BLOCKSYNC = MODE == kBlockSync;
+  constexpr bool TILED = MODE == kTiled;
+  static_assert(!TILED || IPW == 1, "tiled exchange: one island per warp");
+  __shared__ uint4 srec[MODE == kPolled ? 1 : 2 * 32 * IPW];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   uint32_t isl[IPW];
   uint32_t pt[IPW][AP];
   uint64_t ps[IPW][AP];
+  // kTiled: this warp's island, and per direction (lane d < 4) where its
+  // neighbour's record is read: shared-memory slot, or global record.
+  uint32_t nb_island = 0, nb_slot = 0;
+  bool nb_inside = true, publish_global = !BLOCKSYNC;
+  if constexpr (TILED) {
+    const uint32_t ltr = tile & 0xFFu, ltc = tile >> 8;
+    const uint32_t tiles_c = (p.cols + (1u << ltc) - 1) >> ltc;
+    const uint32_t tr = blockIdx.x / tiles_c, tc = blockIdx.x - tr * tiles_c;
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t r = (tr << ltr) + (w >> ltc), c = (tc << ltc) + (w & ((1u << ltc) - 1));
+    const bool active = r < p.rows && c < p.cols;
+    isl[0] = active ? r * p.cols + c : p.islands;
+    if (active && lane < 4) {
+      nb_island = neighbour(p, isl[0], lane);
+      const uint32_t nr = nb_island / p.cols, nc = nb_island - nr * p.cols;
+      nb_inside = (nr >> ltr) == tr && (nc >> ltc) == tc;
+      nb_slot = ((nr & ((1u << ltr) - 1)) << ltc) | (nc & ((1u << ltc) - 1));
+    }
+    publish_global = __any_sync(kFull, !nb_inside);
+  }
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
-    isl[k] = warp * IPW + k;
+    if constexpr (!TILED) isl[k] = warp * IPW + k;
 #pragma unroll
     for (int a = 0; a < AP; ++a) {
       const uint32_t j = lane + 32u * a;
@@ -122,7 +157,8 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
     }
   }
   const bool any_mig = p.interval != 0;
-  bool failed = false;
+  bool failed = false;  // leave now (block-uniform in kTiled)
+  bool wfail = false;   // kTiled: this warp's wait gave up; the block learns at its barrier
 
   for (uint32_t g0 = 0; g0 < ngen && !failed; g0 += kChunk) {
     // Batched per-chunk draws: lane o (< 16) holds the emigrant block of
@@ -152,7 +188,7 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
         // a1: publish every owned island's emigrant before reading any.
 #pragma unroll
         for (int k = 0; k < IPW; ++k) {
-          if (isl[k] >= p.islands) continue;
+          if (isl[k] >= p.islands || wfail) continue;
           const uint32_t eslot = uindex(__shfl_sync(kFull, mig[k].x, o), p.n);
           const uint32_t dir = __shfl_sync(kFull, mig[k].y, o) >> 30;
           if (lane == (eslot & 31u)) {
@@ -167,7 +203,11 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
             if constexpr (BLOCKSYNC) {
               srec[buf * 32 * IPW + isl[k]] =
                   make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
-            } else {
+            } else if (TILED) {
+              srec[buf * 32 + (threadIdx.x >> 5)] =
+                  make_uint4(tv, (uint32_t)sv, (uint32_t)(sv >> 32), dir);
+            }
+            if (publish_global) {
               uint64_t *r = rec + ((size_t)buf * p.islands + isl[k]) * 4;
               const uint64_t stamp = (uint64_t)seq << 32;
               st_relaxed64(r, stamp | tv);
@@ -178,6 +218,14 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
           }
         }
         if constexpr (BLOCKSYNC) __syncthreads();
+        if constexpr (TILED) {
+          // every warp of the tile arrives here once per migration, also
+          // after a failed wait, so the block leaves together
+          if (__syncthreads_or(wfail ? 1 : 0)) {
+            failed = true;
+            break;
+          }
+        }
       }
 #pragma unroll
       for (int k = 0; k < IPW; ++k) {
@@ -190,10 +238,12 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
           uint32_t it = 0;
           uint64_t is = 0;
           if (lane < 4) {
-            const uint32_t nb = neighbour(p, isl[k], lane);
+            const uint32_t nb = TILED ? nb_island : neighbour(p, isl[k], lane);
             uint4 r;
             if constexpr (BLOCKSYNC) {
               r = srec[buf * 32 * IPW + nb];
+            } else if (TILED && nb_inside) {
+              r = srec[buf * 32 + nb_slot];
             } else {
               ok = wait_record(rec + ((size_t)buf * p.islands + nb) * 4, seq, err, &r);
             }
@@ -203,12 +253,21 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
               is = ((uint64_t)r.z << 32) | r.y;
             }
           }
-          if constexpr (!BLOCKSYNC) {
+          if constexpr (MODE == kPolled) {
             if (__any_sync(kFull, !ok)) {
               if (lane == 0) atomicCAS(err, 0, kDevErrWaitTimeout);
               failed = true;
               break;
             }
+          }
+          if constexpr (TILED) {
+            // the warp stops work and goes on to the next barrier, where
+            // the block leaves together
+            if (__any_sync(kFull, !ok)) {
+              if (lane == 0) atomicCAS(err, 0, kDevErrWaitTimeout);
+              wfail = true;
+            }
+            if (wfail) continue;
           }
           const uint32_t arrivals = __ballot_sync(kFull, arrive);
           const uint32_t place[4] = {mig[k].x, mig[k].y, mig[k].z, mig[k].w};
@@ -234,7 +293,7 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
       if (failed) break;
     }
   }
-  if (failed) return;
+  if (failed || wfail) return;
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
 #pragma unroll
@@ -249,17 +308,22 @@ __global__ void __launch_bounds__(BLOCKSYNC ? 1024 : kResidentThreads)
 }
 
 // ------------------------------------------------------------- launch ---
-using ResidentFn = void (*)(RunParams, uint32_t, uint32_t, int, uint32_t *, uint64_t *,
-                            uint64_t *, int *);
+using ResidentFn = void (*)(RunParams, uint32_t, uint32_t, int, uint32_t, uint32_t *,
+                            uint64_t *, uint64_t *, int *);
 
-static ResidentFn pick(int ap, int ipw, bool tracked, bool block) {
+static ResidentFn pick(int ap, int ipw, bool tracked, int mode) {
+#define HSGA_PICK_MODE(AP_, IPW_, MODE_)                                              \
+  if (mode == MODE_)                                                                  \
+    return tracked ? step_resident_kernel<AP_, IPW_, true, MODE_>                     \
+                   : step_resident_kernel<AP_, IPW_, false, MODE_>;
 #define HSGA_PICK(AP_, IPW_)                                                          \
   if (ap == AP_ && ipw == IPW_) {                                                     \
-    if (block)                                                                        \
-      return tracked ? step_resident_kernel<AP_, IPW_, true, true>                    \
-                     : step_resident_kernel<AP_, IPW_, false, true>;                  \
-    return tracked ? step_resident_kernel<AP_, IPW_, true, false>                     \
-                   : step_resident_kernel<AP_, IPW_, false, false>;                   \
+    HSGA_PICK_MODE(AP_, IPW_, kPolled)                                                \
+    HSGA_PICK_MODE(AP_, IPW_, kBlockSync)                                             \
+  }
+  if (ipw == 1 && mode == kTiled) {
+    if (ap == 1) HSGA_PICK_MODE(1, 1, kTiled)
+    if (ap == 2) HSGA_PICK_MODE(2, 1, kTiled)
   }
   HSGA_PICK(1, 1)
   HSGA_PICK(1, 2)
@@ -267,7 +331,41 @@ static ResidentFn pick(int ap, int ipw, bool tracked, bool block) {
   HSGA_PICK(2, 1)
   HSGA_PICK(2, 2)
 #undef HSGA_PICK
+#undef HSGA_PICK_MODE
   return nullptr;
+}
+
+// Tile shape of the kTiled exchange: among tiles of 4 to 32 islands whose
+// blocks are all resident at once, the fewest globally polled neighbour
+// edges per island (ties: the larger tile).  Returns false if none fits.
+static bool pick_tile(const RunParams &p, int ap, bool tracked, int sms, ResidentPlan *out) {
+  ResidentFn fn = pick(ap, 1, tracked, kTiled);
+  if (!fn) return false;
+  double best = 1e30;
+  bool found = false;
+  for (uint32_t lw = 5; lw >= 2; --lw) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 << lw, 0) != cudaSuccess)
+      return false;
+    for (uint32_t ltr = 0; ltr <= lw; ++ltr) {
+      const uint32_t ltc = lw - ltr;
+      const uint64_t tr = 1u << ltr, tc = 1u << ltc;
+      const uint64_t tiles = ((p.rows + tr - 1) / tr) * ((p.cols + tc - 1) / tc);
+      if (per_sm < 1 || tiles > (uint64_t)per_sm * sms) continue;
+      // edges that leave a tile: N and S unless the tile spans every row,
+      // E and W unless it spans every column
+      const double ext = (p.rows > tr ? 2.0 * tc : 0.0) + (p.cols > tc ? 2.0 * tr : 0.0);
+      const double cost = ext / (double)(tr * tc);
+      if (cost < best - 1e-12) {
+        best = cost;
+        found = true;
+        out->blocks = (int)tiles;
+        out->warps_per_block = 1 << lw;
+        out->tile = ltr | (ltc << 8);
+      }
+    }
+  }
+  return found;
 }
 
 bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
@@ -281,7 +379,7 @@ bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
   // small grids: one thread block, shared-memory records, block barriers
   for (int ipw : ipws) {
     if (grid_only) break;
-    ResidentFn fn = pick(ap, ipw, tracked, true);
+    ResidentFn fn = pick(ap, ipw, tracked, kBlockSync);
     if (!fn) continue;
     const uint64_t warps = ((uint64_t)p.islands + ipw - 1) / ipw;
     if (warps > 32) continue;
@@ -294,14 +392,27 @@ bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
       out->ipw = ipw;
       out->blocks = 1;
       out->warps_per_block = (int)warps;
-      out->block_sync = true;
+      out->mode = kBlockSync;
+      out->tile = 0;
       return true;
     }
   }
   if (!coop) return false;
+  if (kResidentTiles) {
+    ResidentPlan t;
+    if (pick_tile(p, ap, tracked, sms, &t)) {
+      out->ap = ap;
+      out->ipw = 1;
+      out->blocks = t.blocks;
+      out->warps_per_block = t.warps_per_block;
+      out->mode = kTiled;
+      out->tile = t.tile;
+      return true;
+    }
+  }
   const int wpb = kResidentThreads / 32;
   for (int ipw : ipws) {
-    ResidentFn fn = pick(ap, ipw, tracked, false);
+    ResidentFn fn = pick(ap, ipw, tracked, kPolled);
     if (!fn) continue;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResidentThreads, 0) !=
@@ -314,7 +425,8 @@ bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
       out->ipw = ipw;
       out->blocks = (int)blocks;
       out->warps_per_block = wpb;
-      out->block_sync = false;
+      out->mode = kPolled;
+      out->tile = 0;
       return true;
     }
   }
@@ -324,17 +436,18 @@ bool resident_plan(const RunParams &p, ResidentPlan *out, bool grid_only) {
 cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, uint32_t G0,
                                  uint32_t ngen, bool premigrated, uint32_t *t, uint64_t *s,
                                  uint64_t *rec, int *err, cudaStream_t stream) {
-  ResidentFn fn = pick(plan.ap, plan.ipw, p.policy != HSGA_NONE, plan.block_sync);
+  ResidentFn fn = pick(plan.ap, plan.ipw, p.policy != HSGA_NONE, plan.mode);
   if (!fn) return cudaErrorInvalidValue;
   RunParams pp = p;
   int prem = premigrated ? 1 : 0;
-  if (plan.block_sync) {
-    fn<<<1, plan.warps_per_block * 32, 0, stream>>>(pp, G0, ngen, prem, t, s, rec, err);
+  uint32_t tile = plan.tile;
+  if (plan.mode == kBlockSync) {
+    fn<<<1, plan.warps_per_block * 32, 0, stream>>>(pp, G0, ngen, prem, tile, t, s, rec, err);
     return cudaGetLastError();
   }
-  void *args[] = {&pp, &G0, &ngen, &prem, &t, &s, &rec, &err};
+  void *args[] = {&pp, &G0, &ngen, &prem, &tile, &t, &s, &rec, &err};
   return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.blocks),
-                                     dim3(kResidentThreads), args, 0, stream);
+                                     dim3(plan.warps_per_block * 32), args, 0, stream);
 }
 
 cudaError_t launch_wait_probe(const uint64_t *record, uint32_t seq, uint64_t limit_ns, int *err,
