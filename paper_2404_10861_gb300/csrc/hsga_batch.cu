@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(512)
     uint32_t *tout = R.trait[par ^ 1u];
     uint64_t *sout = R.surf[par ^ 1u];
     const Deposit dep = deposit_for(p, G);
-    const bool do_mig = migrates(p, G);
+    // 32-bit test, every-generation case first (a 64-bit modulo per work item otherwise)
+    const bool do_mig = p.interval == 1u || (p.interval != 0u && G % p.interval == 0u);
     if (w.isl0 + kGroup <= p.islands) {
       PhiloxHead head[AP];
       replication_heads<AP>(p, G, head);

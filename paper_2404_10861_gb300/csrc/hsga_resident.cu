@@ -30,6 +30,21 @@ namespace hsga {
 
 constexpr uint32_t kChunk = 16;  // generations whose per-island RNG blocks are batched
 
+// Whether generation G migrates, and its migration number G / interval, in
+// 32-bit arithmetic with the every-generation case first: a 64-bit modulo
+// and a division per generation made up about half of the kernel's
+// instructions on the 64x64-island grid.
+__device__ __forceinline__ bool migration_of(const RunParams &p, uint32_t G, uint32_t *m_idx) {
+  if (p.interval == 1u) {
+    *m_idx = G;
+    return true;
+  }
+  if (p.interval == 0u) return false;
+  const uint32_t q = G / p.interval;
+  *m_idx = q;
+  return q * p.interval == G;
+}
+
 __device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t *p) {
   uint64_t v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -75,6 +90,31 @@ __device__ bool wait_record(const uint64_t *r, uint32_t seq, const int *err, uin
     if ((spin & 255u) == 0) {
       if (*(volatile const int *)err != 0) return false;
       if (global_ns() - t0 > limit_ns) return false;
+    }
+  }
+  return false;
+}
+
+// kTiled: the whole warp waits for the records of its island's neighbours
+// in other tiles at once.  Lane 4d + j (< 16) polls word j of the record of
+// direction d (if `polled`: that neighbour lies in another tile), so every
+// poll fetches whole records in one round trip; the wait ends when every
+// polled word carries seq.  Lane 4d + j's word is returned in *word.
+// Bounded like wait_record; returns false (on every lane) when it gave up.
+__device__ bool wait_records_warp(const uint64_t *r, bool polled, uint32_t seq, const int *err,
+                                  uint32_t *word) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t spin = 1; spin < kMaxSpins; ++spin) {
+    bool ready = true;
+    if (polled) {
+      const uint64_t v = ld_relaxed64(r);
+      ready = (uint32_t)(v >> 32) == seq;
+      *word = (uint32_t)v;
+    }
+    if (__all_sync(kFull, ready)) return true;
+    if ((spin & 255u) == 0) {
+      const bool stop = *(volatile const int *)err != 0 || global_ns() - t0 > kWaitNs;
+      if (__any_sync(kFull, stop)) return false;
     }
   }
   return false;
@@ -126,6 +166,8 @@ __global__ void __launch_bounds__(MODE == kPolled ? kResidentThreads : 1024)
   // neighbour's record is read: shared-memory slot, or global record.
   uint32_t nb_island = 0, nb_slot = 0;
   bool nb_inside = true, publish_global = !BLOCKSYNC;
+  const uint64_t *poll_word = nullptr;  // kTiled, lane 4d + j: word j of direction d's record
+  bool polls = false;
   if constexpr (TILED) {
     const uint32_t ltr = tile & 0xFFu, ltc = tile >> 8;
     const uint32_t tiles_c = (p.cols + (1u << ltc) - 1) >> ltc;
@@ -141,6 +183,12 @@ __global__ void __launch_bounds__(MODE == kPolled ? kResidentThreads : 1024)
       nb_slot = ((nr & ((1u << ltr) - 1)) << ltc) | (nc & ((1u << ltc) - 1));
     }
     publish_global = __any_sync(kFull, !nb_inside);
+    // lane 4d + j polls word j of direction d's record (both buffers: +buf offset)
+    const uint32_t d = (lane >> 2) & 3u;
+    const uint32_t nb_d = __shfl_sync(kFull, nb_island, d);
+    const bool inside_d = __shfl_sync(kFull, nb_inside, d);
+    polls = lane < 16 && !inside_d;
+    poll_word = rec + (size_t)nb_d * 4 + (lane & 3u);
   }
 #pragma unroll
   for (int k = 0; k < IPW; ++k) {
@@ -179,10 +227,10 @@ __global__ void __launch_bounds__(MODE == kPolled ? kResidentThreads : 1024)
       const uint32_t G = G0 + g0 + o;
       const uint32_t dp = __shfl_sync(kFull, dpack, o);
       const Deposit dep = deposit_unpack(dp, (uint32_t)p.vmask);
-      const bool do_mig = migrates(p, G) && !(premigrated && g0 + o == 0);
+      uint32_t m_idx = 0;
+      const bool do_mig = migration_of(p, G, &m_idx) && !(premigrated && g0 + o == 0);
       uint32_t buf = 0, seq = 0;
       if (do_mig) {
-        const uint32_t m_idx = G / p.interval;
         buf = m_idx & 1u;
         seq = m_idx + 1u;
         // a1: publish every owned island's emigrant before reading any.
@@ -237,13 +285,29 @@ __global__ void __launch_bounds__(MODE == kPolled ? kResidentThreads : 1024)
           bool ok = true, arrive = false;
           uint32_t it = 0;
           uint64_t is = 0;
-          if (lane < 4) {
-            const uint32_t nb = TILED ? nb_island : neighbour(p, isl[k], lane);
+          if constexpr (TILED) {
+            // records from other tiles: one warp-wide wait, then lane d
+            // gathers the four words of direction d
+            uint32_t word = 0;
+            ok = wait_records_warp(poll_word + (size_t)buf * p.islands * 4, polls, seq, err,
+                                   &word);
+            const uint32_t src = (lane & 3u) << 2;
+            const uint32_t g0 = __shfl_sync(kFull, word, src);
+            const uint32_t g1 = __shfl_sync(kFull, word, src + 1);
+            const uint32_t g2 = __shfl_sync(kFull, word, src + 2);
+            const uint32_t g3 = __shfl_sync(kFull, word, src + 3);
+            if (lane < 4 && ok) {
+              uint4 r = make_uint4(g0, g1, g2, g3);
+              if (nb_inside) r = srec[buf * 32 + nb_slot];
+              arrive = r.w == ((lane + 2u) & 3u);
+              it = r.x;
+              is = ((uint64_t)r.z << 32) | r.y;
+            }
+          } else if (lane < 4) {
+            const uint32_t nb = neighbour(p, isl[k], lane);
             uint4 r;
             if constexpr (BLOCKSYNC) {
               r = srec[buf * 32 * IPW + nb];
-            } else if (TILED && nb_inside) {
-              r = srec[buf * 32 + nb_slot];
             } else {
               ok = wait_record(rec + ((size_t)buf * p.islands + nb) * 4, seq, err, &r);
             }
