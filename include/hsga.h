@@ -348,13 +348,15 @@ int hsga_lookup(uint32_t policy, uint32_t S, uint32_t W, uint64_t T,
 int hsga_sites_device(uint32_t policy, uint32_t S, uint32_t W, uint64_t T0,
                       uint64_t count, uint32_t *out_dev, void *cuda_stream);
 
-/* The bounded wait the resident kernel applies to its neighbours' migrant
- * records, run by one GPU thread on a caller's record: waits until all four
- * 64-bit words of record_dev carry seq in their high 32 bits, giving up after
- * limit_ns (<= 1 s) of the GPU's global timer or 2^22 polls.  Returns
- * HSGA_OK when the record arrived, HSGA_ERR_WAIT_TIMEOUT when the wait gave
- * up (the context stays usable); *waited_ns (may be NULL) receives the time
- * spent.  record_dev: device, 4 uint64, 8-byte aligned.  Synchronous on
+/* The bounded waits the resident kernel applies to its neighbours' migrant
+ * records, run on a caller's record: waits until all four 64-bit words of
+ * record_dev carry seq in their high 32 bits, giving up after limit_ns
+ * (<= 1 s) of the GPU's global timer or 2^22 polls -- first in the form one
+ * thread runs (islands polling each neighbour), then in the form a whole
+ * warp runs (tiles of islands polling their neighbouring tiles; four lanes,
+ * one word each).  Returns HSGA_OK when both saw the record arrive,
+ * HSGA_ERR_WAIT_TIMEOUT when either gave up (the context stays usable);
+ * *waited_ns (may be NULL) receives the time spent in both.  record_dev: device, 4 uint64, 8-byte aligned.  Synchronous on
  * cuda_stream.  For checking that an unmet wait ends with a status instead of
  * hanging. */
 int hsga_wait_probe(const uint64_t *record_dev, uint32_t seq, uint64_t limit_ns,

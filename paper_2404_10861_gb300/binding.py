@@ -318,8 +318,9 @@ def hsga_reconstruct(surf, policy, bits: int, W: int, generations: int, coarsen:
 
 
 def hsga_wait_probe(record_dev, seq: int, limit_ns: int, stream=None):
-    """Runs the resident kernel's bounded wait on a device record of four
-    64-bit words; returns (status, waited_ns) without raising on a timeout."""
+    """Runs the resident kernel's bounded waits (one thread's, then a
+    warp's) on a device record of four 64-bit words; returns (status,
+    waited_ns) without raising on a timeout."""
     waited = ctypes.c_uint64(0)
     s = None if stream is None else ctypes.c_void_p(int(stream))
     st = lib().hsga_wait_probe(_ptr(record_dev), seq, limit_ns, ctypes.byref(waited), s)

@@ -102,7 +102,7 @@ __device__ bool wait_record(const uint64_t *r, uint32_t seq, const int *err, uin
 // polled word carries seq.  Lane 4d + j's word is returned in *word.
 // Bounded like wait_record; returns false (on every lane) when it gave up.
 __device__ bool wait_records_warp(const uint64_t *r, bool polled, uint32_t seq, const int *err,
-                                  uint32_t *word) {
+                                  uint32_t *word, uint64_t limit_ns = kWaitNs) {
   const uint64_t t0 = global_ns();
   for (uint32_t spin = 1; spin < kMaxSpins; ++spin) {
     bool ready = true;
@@ -113,23 +113,34 @@ __device__ bool wait_records_warp(const uint64_t *r, bool polled, uint32_t seq, 
     }
     if (__all_sync(kFull, ready)) return true;
     if ((spin & 255u) == 0) {
-      const bool stop = *(volatile const int *)err != 0 || global_ns() - t0 > kWaitNs;
+      const bool stop = *(volatile const int *)err != 0 || global_ns() - t0 > limit_ns;
       if (__any_sync(kFull, stop)) return false;
     }
   }
   return false;
 }
 
-// One thread runs wait_record on a caller's record (hsga_wait_probe): out[0]
-// = 1 if the record carried seq, 0 if the wait gave up; out[1] = nanoseconds
-// spent.
+// Both forms of the wait on a caller's record (hsga_wait_probe), in turn:
+// lane 0 alone runs wait_record, then the whole warp runs wait_records_warp
+// with lanes 0..3 polling words 0..3.  out[0] = 1 if both saw the record
+// carry seq, 0 if either gave up; out[1] = nanoseconds spent in all.
 __global__ void wait_probe_kernel(const uint64_t *record, uint32_t seq, uint64_t limit_ns,
                                   int *err, uint64_t *out) {
+  const uint32_t lane = threadIdx.x & 31u;
   const uint64_t t0 = global_ns();
-  uint4 r;
-  const bool ok = wait_record(record, seq, err, &r, limit_ns);
-  out[0] = ok ? 1u : 0u;
-  out[1] = global_ns() - t0;
+  bool ok = true;
+  if (lane == 0) {
+    uint4 r;
+    ok = wait_record(record, seq, err, &r, limit_ns);
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  uint32_t word = 0;
+  const bool ok_warp =
+      wait_records_warp(record + (lane & 3u), lane < 4, seq, err, &word, limit_ns);
+  if (lane == 0) {
+    out[0] = (ok && ok_warp) ? 1u : 0u;
+    out[1] = global_ns() - t0;
+  }
 }
 
 // Three ways of exchanging the emigrant records (MODE):
@@ -516,7 +527,7 @@ cudaError_t launch_step_resident(const RunParams &p, const ResidentPlan &plan, u
 
 cudaError_t launch_wait_probe(const uint64_t *record, uint32_t seq, uint64_t limit_ns, int *err,
                               uint64_t *out, cudaStream_t stream) {
-  wait_probe_kernel<<<1, 1, 0, stream>>>(record, seq, limit_ns, err, out);
+  wait_probe_kernel<<<1, 32, 0, stream>>>(record, seq, limit_ns, err, out);
   return cudaGetLastError();
 }
 

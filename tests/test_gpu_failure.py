@@ -1,7 +1,8 @@
-"""Failure detection without a GPU fault: the bounded wait the resident
-kernel applies to its neighbours' stamped records, run on a record that
-nothing writes, must end with HSGA_ERR_WAIT_TIMEOUT near its limit and leave
-the context usable; on a record that carries the stamp it must return at
+"""Failure detection without a GPU fault: the bounded waits the resident
+kernel applies to its neighbours' stamped records (one thread's, and the
+warp-wide form of the tiled exchange), run on a record that nothing writes,
+must each end with HSGA_ERR_WAIT_TIMEOUT near their limit and leave the
+context usable; on a record that carries the stamp they must return at
 once."""
 import numpy as np
 import pytest
@@ -26,10 +27,14 @@ def test_unmet_wait_times_out_and_context_survives(hb, orc):
     limit = 20_000_000                                      # 20 ms
     status, waited = hb.hsga_wait_probe(record, 1, limit)
     assert status == WAIT_TIMEOUT
-    assert limit <= waited < limit + 200_000_000
+    assert 2 * limit <= waited < 2 * limit + 200_000_000   # both forms ran out
     record.copy_(torch.tensor([(3 << 32) | v for v in (11, 12, 13, 2)], dtype=torch.int64))
     status, waited = hb.hsga_wait_probe(record, 3, limit)
     assert status == 0 and waited < limit
+    record[1] = (4 << 32) | 12                              # one word of a newer record
+    status, waited = hb.hsga_wait_probe(record, 3, limit)
+    assert status == WAIT_TIMEOUT and waited >= 2 * limit
+    record[1] = (3 << 32) | 12
     record[2] = (2 << 32) | 13                              # one word of an older record
     status, _ = hb.hsga_wait_probe(record, 3, limit)
     assert status == WAIT_TIMEOUT
