@@ -194,12 +194,30 @@ __device__ __forceinline__ uint32_t owned_octets(uint32_t warp, uint32_t nwarps,
 }
 
 // ------------------------------------------------- latest-emigrant mode ---
+// Migration draws of several octet generations in one Philox pass: lane
+// 2 IPW e + b holds, for batch element e (the next octets of this warp, or
+// the next generations of one octet) with first island first_e at
+// generation G_e, the emigrant block of island first_e + b (b < IPW) or the
+// placement block of island first_e + b - IPW.
+template <int IPW>
+constexpr uint32_t kMigBatch = 32u / (2u * IPW);
+
+template <int IPW>
+__device__ __forceinline__ Words4 migration_blocks(const RunParams &p, uint32_t lane,
+                                                   uint32_t first_e, uint32_t G_e) {
+  const uint32_t b = lane % (2u * IPW);
+  return philox_rk(p, b >= (uint32_t)IPW ? kSlotImmigrant : kSlotEmigrant,
+                   first_e + b % (uint32_t)IPW, G_e, kPurposeMigration);
+}
+
 // One generation of one octet: lane 4k + j publishes word j of island k's
 // emigrant record, and lane 4k + d reads the record of island k's neighbour
-// in direction d (`seen`: the newest stamp it has seen from it).
+// in direction d (`seen`: the newest stamp it has seen from it).  m: this
+// generation's migration blocks from migration_blocks, at lanes msrc + b.
 template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
 __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> &o,
                                                  uint32_t &seen, uint32_t lane, uint32_t G,
+                                                 const Words4 &m, uint32_t msrc,
                                                  uint64_t *rec, uint32_t *log,
                                                  uint32_t log_G0, uint32_t log_gens) {
   const uint32_t n = NN ? (uint32_t)NN : p.n, first = o.first;
@@ -208,17 +226,12 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
   const uint32_t risl = first + rk;
   const bool logging = log && G >= log_G0 && G - log_G0 < log_gens;
   if (migrates32(p, G)) {
-    // block lane b: b < IPW the emigrant block of island b, IPW <= b < 2 IPW
-    // the placement block of island b - IPW
-    const uint32_t bk = lane < (uint32_t)IPW ? lane : (lane < 2u * IPW ? lane - IPW : 0u);
-    const Words4 m = philox_rk(p, lane >= (uint32_t)IPW ? kSlotImmigrant : kSlotEmigrant,
-                               first + bk, G, kPurposeMigration);
     // a1: lane 4k + j gathers word j of island k's emigrant and publishes it
     uint32_t word = 0, dir = 0;
 #pragma unroll
     for (int k = 0; k < IPW; ++k) {
-      const uint32_t eslot = uindex_nn<NN>(__shfl_sync(kFull, m.x, k), n);
-      const uint32_t dk = __shfl_sync(kFull, m.y, k) >> 30;
+      const uint32_t eslot = uindex_nn<NN>(__shfl_sync(kFull, m.x, msrc + k), n);
+      const uint32_t dk = __shfl_sync(kFull, m.y, msrc + k) >> 30;
       const uint32_t vt = __shfl_sync(kFull, o.t[k], eslot);
       const uint64_t vs = shfl64(o.s[k], eslot);
       const uint32_t vT = __shfl_sync(kFull, o.T[k], eslot);
@@ -260,8 +273,8 @@ __device__ __forceinline__ void async_generation(const RunParams &p, Octet<IPW> 
 #pragma unroll
       for (uint32_t dd = 0; dd < 4; ++dd) {
         if (bits & (1u << dd)) {
-          const uint32_t slot =
-              uindex_nn<NN>(__shfl_sync(kFull, pick4(m.x, m.y, m.z, m.w, dd), IPW + k), n);
+          const uint32_t slot = uindex_nn<NN>(
+              __shfl_sync(kFull, pick4(m.x, m.y, m.z, m.w, dd), msrc + IPW + k), n);
           const uint32_t src = 4u * k + dd;
           const uint32_t vt = __shfl_sync(kFull, r[0], src);
           const uint64_t vs = shfl64(is, src);
@@ -317,9 +330,16 @@ __global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
           load_octet<TRACKED, IPW, NN>(p, o, first, lane, tplane, splane, Tplane);
           seen = reader ? seen_io[(first + rk) * 4 + rd] : 0u;
         }
-        for (uint32_t g = g0; g < g0 + gl; ++g)
-          async_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, seen, lane, G0 + g, rec, log,
-                                                           log_G0, log_gens);
+        Words4 m{0u, 0u, 0u, 0u};
+        for (uint32_t g = g0; g < g0 + gl; ++g) {
+          // migration draws batched over the next generations of this octet
+          const uint32_t q = (g - g0) % kMigBatch<IPW>;
+          if (q == 0 && p.interval != 0u)
+            m = migration_blocks<IPW>(p, lane, first, G0 + g + lane / (2u * IPW));
+          async_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, seen, lane, G0 + g, m,
+                                                           q * 2u * IPW, rec, log, log_G0,
+                                                           log_gens);
+        }
         if (owned > 1 || g0 + gl == ngen) {
           store_octet<TRACKED, IPW, NN>(p, o, lane, tplane, splane, Tplane);
           if (reader) seen_io[(first + rk) * 4 + rd] = seen;
@@ -327,6 +347,10 @@ __global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
       }
     }
   } else {
+    // migration draws batched over this warp's next octets (or, for a warp
+    // with a single octet, over its next generations)
+    const bool batch_octets = owned > 1;
+    Words4 m{0u, 0u, 0u, 0u};
     for (uint32_t g = 0; g < ngen; ++g) {
       for (uint32_t j = 0; j < owned; ++j) {
         const uint32_t first = (warp + j * nwarps) * IPW;
@@ -335,8 +359,16 @@ __global__ void __launch_bounds__(kResidentThreads, kAsyncBlocksPerSM)
           load_octet<TRACKED, IPW, NN>(p, o, first, lane, tplane, splane, Tplane);
           seen = reader ? seen_io[(first + rk) * 4 + rd] : 0u;
         }
-        async_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, seen, lane, G0 + g, rec, log,
-                                                         log_G0, log_gens);
+        const uint32_t q = (batch_octets ? j : g) % kMigBatch<IPW>;
+        if (q == 0 && p.interval != 0u) {
+          const uint32_t e = lane / (2u * IPW);
+          m = batch_octets
+                  ? migration_blocks<IPW>(p, lane, (warp + (j + e) * nwarps) * IPW, G0 + g)
+                  : migration_blocks<IPW>(p, lane, first, G0 + g + e);
+        }
+        async_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, seen, lane, G0 + g, m,
+                                                         q * 2u * IPW, rec, log, log_G0,
+                                                         log_gens);
         if (owned > 1 || g + 1 == ngen) {
           store_octet<TRACKED, IPW, NN>(p, o, lane, tplane, splane, Tplane);
           if (reader) seen_io[(first + rk) * 4 + rd] = seen;
@@ -371,10 +403,28 @@ struct LaneChannel {
   uint32_t posts, taken, waiting;
 };
 
-template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0>
+// Emigrant draws of several generations of one octet in one Philox pass
+// (octet slices): lane IPW e + k holds the emigrant block of island
+// first + k at generation G + e.
+template <int IPW>
+constexpr uint32_t kSendBatch = 32u / IPW;
+
+template <int IPW>
+__device__ __forceinline__ Words4 emigrant_blocks(const RunParams &p, uint32_t lane,
+                                                  uint32_t first, uint32_t G) {
+  return philox_rk(p, kSlotEmigrant, first + lane % (uint32_t)IPW, G + lane / (uint32_t)IPW,
+                   kPurposeMigration);
+}
+
+// BATCHED: the emigrant blocks come from emigrant_blocks (wb, this
+// generation's at lanes wsrc + k); otherwise each lane draws its island's
+// block itself (one block per generation, fewer registers held across
+// octets: 193 against 208 us per generation at 16.8M agents).
+template <bool TRACKED, bool T2, bool TWO, int IPW, bool FLT, int NN = 0, bool BATCHED = false>
 __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IPW> &o,
                                                     LaneChannel &ch, uint32_t lane, uint32_t G,
-                                                    bool mig, uint64_t *mail, uint32_t *ack,
+                                                    bool mig, const Words4 &wb, uint32_t wsrc,
+                                                    uint64_t *mail, uint32_t *ack,
                                                     uint4 *inbuf, uint32_t *log,
                                                     uint32_t log_G0, uint32_t log_gens) {
   const uint32_t n = NN ? (uint32_t)NN : p.n;
@@ -453,8 +503,17 @@ __device__ __forceinline__ void buffered_generation(const RunParams &p, Octet<IP
     // send on every channel whose previous post was acknowledged
     const bool send = (sends >> lane) & 1u;
     if (sends) {
-      const Words4 w = philox_rk(p, kSlotEmigrant, me, G, kPurposeMigration);
-      const uint32_t slot = uindex_nn<NN>(pick4(w.x, w.y, w.z, w.w, rd), n);
+      uint32_t slot;
+      if constexpr (BATCHED) {
+        // word d of island k's emigrant block, from lane wsrc + k
+        const uint32_t src = wsrc + (rk & (uint32_t)(IPW - 1));
+        const uint32_t wx = __shfl_sync(kFull, wb.x, src), wy = __shfl_sync(kFull, wb.y, src);
+        const uint32_t wz = __shfl_sync(kFull, wb.z, src), ww = __shfl_sync(kFull, wb.w, src);
+        slot = uindex_nn<NN>(pick4(wx, wy, wz, ww, rd), n);
+      } else {
+        const Words4 w = philox_rk(p, kSlotEmigrant, me, G, kPurposeMigration);
+        slot = uindex_nn<NN>(pick4(w.x, w.y, w.z, w.w, rd), n);
+      }
       uint32_t et = 0, eT = 0;
       uint64_t es = 0;
 #pragma unroll
@@ -516,10 +575,15 @@ __global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
             ch = LaneChannel{st.x, st.y, st.z};
           }
         }
-        for (uint32_t g = g0; g < g0 + gl; ++g)
-          buffered_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, ch, lane, G0 + g,
-                                                              migrates32(p, G0 + g), mail, ack,
-                                                              inbuf, log, log_G0, log_gens);
+        Words4 wb{0u, 0u, 0u, 0u};
+        for (uint32_t g = g0; g < g0 + gl; ++g) {
+          // emigrant draws batched over the next generations of this octet
+          const uint32_t q = (g - g0) % kSendBatch<IPW>;
+          if (q == 0 && p.interval != 0u) wb = emigrant_blocks<IPW>(p, lane, first, G0 + g);
+          buffered_generation<TRACKED, T2, TWO, IPW, FLT, NN, true>(
+              p, o, ch, lane, G0 + g, migrates32(p, G0 + g), wb, q * IPW, mail, ack, inbuf, log,
+              log_G0, log_gens);
+        }
         if (owned > 1 || g0 + gl == ngen) {
           store_octet<TRACKED, IPW, NN>(p, o, lane, tplane, splane, Tplane);
           if (mine) chst[c] = make_uint4(ch.posts, ch.taken, ch.waiting, 0u);
@@ -540,7 +604,8 @@ __global__ void __launch_bounds__(kResidentThreads, kBufferedBlocksPerSM)
             ch = LaneChannel{st.x, st.y, st.z};
           }
         }
-        buffered_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, ch, lane, G0 + g, mig, mail,
+        buffered_generation<TRACKED, T2, TWO, IPW, FLT, NN>(p, o, ch, lane, G0 + g, mig,
+                                                            Words4{0u, 0u, 0u, 0u}, 0u, mail,
                                                             ack, inbuf, log, log_G0, log_gens);
         if (owned > 1 || g + 1 == ngen) {
           store_octet<TRACKED, IPW, NN>(p, o, lane, tplane, splane, Tplane);
