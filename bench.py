@@ -602,10 +602,12 @@ def run_served(args):
     reqs = serve.poisson_requests(args.requests, rate, seed=5, gen_scale=args.gen_scale)
     offered = sum(r.agents * r.generations for r in reqs) / reqs[-1].arrival
     stream = torch.cuda.Stream()
+    large_stream = torch.cuda.Stream()     # large runs' own grids, beside the batch
     # the device's own memory is the cap unless one is given
     cap = (args.memory_cap_mb * 2**20 if args.memory_cap_mb
            else int(0.9 * torch.cuda.mem_get_info()[0]))
-    res_b, st_b = serve.serve(reqs, memory_cap=cap, stream=stream.cuda_stream)
+    res_b, st_b = serve.serve(reqs, memory_cap=cap, stream=stream.cuda_stream,
+                              large_stream=large_stream.cuda_stream)
     res_a, st_a = serve.serve_alone(reqs, stream=stream.cuda_stream)
     same = sum(int(np.array_equal(a.words, b.words) and np.array_equal(a.where, b.where))
                for a, b in zip(sorted(res_a, key=lambda r: r.rid),
@@ -617,7 +619,8 @@ def run_served(args):
                     f"log-uniform [1000, 100000] / {args.gen_scale}, random policy and "
                     f"adaptive flag, seed 5, 10,000-genome samples",
         "admission": "size-aware: runs of >= 2^20 agents one at a time (first come, first "
-                     "served among them), smaller runs first come, first served as they fit",
+                     "served among them) on their own grid beside the batch, smaller runs "
+                     "first come, first served into the batch as they fit",
         "offered_agent_replications_per_s": offered,
         "memory_cap_bytes": cap,
         "served": serve.summarize(res_b, st_b), "alone": serve.summarize(res_a, st_a),

@@ -14,11 +14,13 @@ Admission is size-aware.  A run of at least ``large_agents`` agents keeps
 the whole GPU busy on its own; at most ``max_large`` of those run at a time,
 first come first served among them, while smaller requests are admitted in
 arrival order as soon as they fit, never queueing behind a large one.  A
-large run then advances at nearly its speed alone (the small runs sharing
-its ticks add little work), and small runs, which alone would leave the GPU
-idle between their short generations, overlap with it.  ``serve_alone`` is
-the reference policy: the same stream served one request at a time, each on
-its own grid.
+large run advances on a grid of its own (the single-run kernels, which
+stream a large grid faster than the batch's tick kernel) on a second stream
+beside the batch, in slices of the same length as the batch's, so it runs
+at nearly its speed alone; the small runs, which alone would leave the GPU
+idle between their short generations, overlap with it in the batch.
+``serve_alone`` is the reference policy: the same stream served one request
+at a time, each on its own grid.
 
 Every run's result is the same whether it ran alone or in the mix (the batch
 engine is bit-identical to a lone grid); tests check that on sampled output.
@@ -103,29 +105,40 @@ def _wait_until(t0: float, rel: float):
 
 
 def serve(requests, memory_cap: int, slice_ticks: int = 256, stream=None,
-          large_agents: int | None = 1 << 20, max_large: int = 1):
+          large_agents: int | None = 1 << 20, max_large: int = 1, large_apart: bool = True,
+          large_stream=None):
     """Continuous batching with size-aware admission (module docstring);
     large_agents=None admits every request first come, first served.
-    Returns (results, stats)."""
+    large_apart=False keeps large runs inside the batch too.  large_stream:
+    the stream of the large runs' grids (default: `stream`, which serialises
+    them with the batch).  Returns (results, stats)."""
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting: list = []                 # arrived, not admitted, in arrival order
-    running = {}                       # run id -> (request, admitted time, footprint)
+    running = {}                       # batch run id -> (request, admitted time, footprint)
+    apart = {}                         # request id -> [request, admitted, footprint, grid, done]
     results = []
     in_use = 0
     peak_runs = 0
     peak_large = 0
     blocked = 0                        # admissions deferred by the memory cap
+    grid_launches = 0
+    if large_stream is None:
+        large_stream = stream
 
     def is_large(req):
         return large_agents is not None and req.agents >= large_agents
 
+    def finish(req, admitted, words, where):
+        results.append(Result(req.rid, req.arrival, admitted, time.perf_counter() - t0,
+                              req.agents * req.generations, words, where))
+
     with hb.Batch(stream=stream) as batch:
         t0 = time.perf_counter()
-        while pending or waiting or running:
+        while pending or waiting or running or apart:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            large_now = sum(1 for req, _, _ in running.values() if is_large(req))
+            large_now = len(apart) + sum(1 for req, _, _ in running.values() if is_large(req))
             i = 0
             while i < len(waiting):
                 req = waiting[i]
@@ -139,33 +152,52 @@ def serve(requests, memory_cap: int, slice_ticks: int = 256, stream=None,
                     blocked += 1
                     break                  # memory goes to requests in arrival order
                 waiting.pop(i)
-                rid = batch.add(req.generations, **req.config)
-                running[rid] = (req, time.perf_counter() - t0, fp)
+                admitted = time.perf_counter() - t0
+                if large_apart and is_large(req):
+                    apart[req.rid] = [req, admitted, fp, hb.Grid(stream=large_stream,
+                                                                 **req.config), 0]
+                else:
+                    rid = batch.add(req.generations, **req.config)
+                    running[rid] = (req, admitted, fp)
                 in_use += fp
                 large_now += is_large(req)
-            peak_runs = max(peak_runs, len(running))
+            peak_runs = max(peak_runs, len(running) + len(apart))
             peak_large = max(peak_large, large_now)
-            if not running:
+            if not running and not apart:
                 if pending:
                     _wait_until(t0, pending[0].arrival)
                 continue
-            remaining = min(req.generations - batch.info(rid)["generation"]
-                            for rid, (req, _, _) in running.items())
-            batch.run(max(1, min(slice_ticks, remaining)))
+            # one slice: the large runs' grids and the batch advance side by side
+            for a in apart.values():
+                n = min(slice_ticks, a[0].generations - a[4])
+                a[3].run(n)
+                a[4] += n
+            if running:
+                remaining = min(req.generations - batch.info(rid)["generation"]
+                                for rid, (req, _, _) in running.items())
+                batch.run(max(1, min(slice_ticks, remaining)))
+            for a in apart.values():
+                a[3].sync()
             batch.sync()          # one slice in flight: arrivals join at the next slice
+            for key in [k for k, a in apart.items() if a[4] >= a[0].generations]:
+                req, admitted, fp, g, _ = apart.pop(key)
+                words, where = g.sample(req.sample_k)              # synchronous
+                grid_launches += g.stats()["kernel_launches"]
+                g.close()
+                finish(req, admitted, words, where)
+                in_use -= fp
             for rid in [r for r in running if batch.info(r)["done"]]:
                 req, admitted, fp = running.pop(rid)
                 words, where = batch.sample(rid, req.sample_k)       # synchronous
-                results.append(Result(req.rid, req.arrival, admitted,
-                                      time.perf_counter() - t0,
-                                      req.agents * req.generations, words, where))
+                finish(req, admitted, words, where)
                 batch.remove(rid)
                 in_use -= fp
         elapsed = time.perf_counter() - t0
         st = batch.stats()
     return results, {"elapsed_s": elapsed, "peak_concurrent_runs": peak_runs,
                      "peak_concurrent_large_runs": peak_large,
-                     "admissions_deferred": blocked, "kernel_launches": st["kernel_launches"],
+                     "admissions_deferred": blocked,
+                     "kernel_launches": st["kernel_launches"] + grid_launches,
                      "ticks": st["tick"]}
 
 

@@ -56,3 +56,32 @@ def test_served_results_equal_alone_and_oracle_under_memory_cap(hb, orc, oracle_
             assert np.array_equal(r.where, owhere), ("oracle", r.rid)
     summ = serve.summarize(res_b, st_b)
     assert summ["latency_p99_s"] >= summ["latency_p50_s"] > 0
+
+
+def test_large_requests_advance_on_their_own_grid_beside_the_batch(hb, orc, oracle_pool):
+    """Requests of at least 2^20 agents run one at a time on a grid of their
+    own, on a second stream beside the batch; every result equals the
+    request run alone, and the first large one also the oracle's."""
+    import torch
+    from paper_2404_10861_gb300 import serve
+    small = serve.poisson_requests(10, rate=4000.0, seed=7, gen_scale=100,
+                                   agents_range=(1024, 16384), sample_k=64)
+    big = dict(rows=256, cols=128, n=32, tournament=2, policy="tilted", bits=1, W=2,
+               interval=1, p_ben=1e-3, p_del=0.0)                 # 2^20 agents
+    bigs = [serve.Request(100 + i, 0.0005 * i, dict(big, seed=77 + i), 120 + 40 * i, 64)
+            for i in range(2)]
+    want = oracle_pool.submit(oracle_result, bigs[0].config, bigs[0].generations, 64)
+    reqs = small + bigs
+    stream, large = torch.cuda.Stream(), torch.cuda.Stream()
+    res_b, st_b = serve.serve(reqs, memory_cap=1 << 36, slice_ticks=32,
+                              stream=stream.cuda_stream, large_stream=large.cuda_stream)
+    res_a, _ = serve.serve_alone(reqs)
+    assert len(res_b) == len(reqs) == len(res_a)
+    assert st_b["peak_concurrent_large_runs"] == 1
+    by_id = {r.rid: r for r in res_a}
+    for r in res_b:
+        assert np.array_equal(r.words, by_id[r.rid].words), r.rid
+        assert np.array_equal(r.where, by_id[r.rid].where), r.rid
+    ow, owhere = want.result()
+    got = {r.rid: r for r in res_b}[bigs[0].rid]
+    assert np.array_equal(got.words, ow) and np.array_equal(got.where, owhere)

@@ -64,6 +64,33 @@ class FakeBatch:
         return {"kernel_launches": 0, "tick": self.ticks}
 
 
+class FakeGrid:
+    """Stands in for binding.Grid (a large run advancing on its own grid)."""
+
+    def __init__(self, stream=None, **cfg):
+        self.cfg = cfg
+        self.gen = 0
+        FakeBatch.log.append(("grid", cfg["seed"]))
+
+    def run(self, n):
+        assert n >= 1
+        self.gen += n
+        FakeBatch.log.append(("grid_run", self.cfg["seed"], n))
+
+    def sync(self):
+        pass
+
+    def sample(self, k):
+        words = np.full((k, 4), self.cfg["seed"] & 0xFFFFFFFF, dtype=np.uint32)
+        return words, np.zeros((k, 2), dtype=np.uint32)
+
+    def stats(self):
+        return {"kernel_launches": self.gen}
+
+    def close(self):
+        FakeBatch.log.append(("grid_close", self.cfg["seed"]))
+
+
 def footprint(cfg):
     """The fake's device bytes: two 12-byte planes per agent plus records."""
     islands = cfg["rows"] * cfg["cols"]
@@ -73,6 +100,7 @@ def footprint(cfg):
 @pytest.fixture
 def fake(monkeypatch):
     monkeypatch.setattr(serve.hb, "Batch", FakeBatch)
+    monkeypatch.setattr(serve.hb, "Grid", FakeGrid)
     monkeypatch.setattr(serve.hb, "make_config", lambda **cfg: cfg)
     monkeypatch.setattr(serve.hb, "hsga_run_footprint", footprint)
     return FakeBatch
@@ -164,19 +192,45 @@ def test_request_stream_follows_its_recipe():
 
 def test_large_runs_one_at_a_time_and_small_ones_pass_them(fake):
     """Size-aware admission: requests of at least large_agents agents run one
-    at a time in arrival order, and a small request that arrives behind a
-    waiting large one is admitted at once."""
+    at a time in arrival order, each on a grid of its own advanced in slices
+    beside the batch, and a small request that arrives behind a waiting large
+    one is admitted at once."""
     big = 256            # 256 x 256 islands x 32 agents = 2.1M agents: large
     reqs = [request(0, 0.0, big, 300), request(1, 0.0, big, 200), request(2, 0.0, 8, 50),
             request(3, 0.0, big, 100), request(4, 0.0, 16, 80)]
     results, stats = serve.serve(reqs, memory_cap=1 << 34, slice_ticks=64,
                                  large_agents=1 << 20)
     assert sorted(r.rid for r in results) == list(range(5))
+    for r in results:
+        assert (r.words == reqs[r.rid].config["seed"]).all()
+        assert r.replications == reqs[r.rid].agents * reqs[r.rid].generations
     assert stats["peak_concurrent_large_runs"] == 1
+    assert stats["kernel_launches"] == 300 + 200 + 100     # the fake grids' generations
     seeds = {r.config["seed"]: r for r in reqs}
+    admitted = [seeds[ev[-1] if ev[0] == "add" else ev[1]].rid for ev in fake.log
+                if ev[0] in ("add", "grid")]
+    assert admitted.index(2) < admitted.index(1) and admitted.index(4) < admitted.index(1)
+    assert [a for a in admitted if reqs[a].agents >= 1 << 20] == [0, 1, 3]
+    # large runs never enter the batch; each advances in slices of at most 64
+    # generations to its budget; never two large grids open at once
+    assert all(seeds[ev[2]].agents < 1 << 20 for ev in fake.log if ev[0] == "add")
+    live, total = 0, {}
+    for ev in fake.log:
+        if ev[0] == "grid":
+            live += 1
+        elif ev[0] == "grid_close":
+            live -= 1
+        elif ev[0] == "grid_run":
+            assert ev[2] <= 64
+            total[ev[1]] = total.get(ev[1], 0) + ev[2]
+        assert live <= 1
+    assert total == {1000: 300, 1001: 200, 1003: 100}
+    # inside the batch instead (large_apart=False), still one large run at a time
+    serve.serve(reqs, memory_cap=1 << 34, slice_ticks=64, large_agents=1 << 20,
+                large_apart=False)
     adds = [seeds[ev[2]].rid for ev in fake.log if ev[0] == "add"]
-    assert adds.index(2) < adds.index(1) and adds.index(4) < adds.index(1)
     assert [a for a in adds if reqs[a].agents >= 1 << 20] == [0, 1, 3]
+    assert not any(ev[0] == "grid" for ev in fake.log)
     live_large, rid_to_req = 0, {}
     for ev in fake.log:                     # never two large runs live at once
         if ev[0] == "add":
