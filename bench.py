@@ -541,16 +541,9 @@ def batched_runs(gen_scale: int, count: int = 256, master: int = 4):
     return runs
 
 
-BATCH_LARGE_ISLANDS = 16384    # a run of this many islands fills the GPU on its own
-
-
 def run_batched(args):
-    """Batched replicates against the same runs launched one after another
-    through the plain grid API, batched two ways: every run in one batch;
-    and the runs that fill the GPU on their own (>= 16,384 islands) one after
-    another on their own grids (the single-run kernels) on a second stream,
-    from a second host thread, beside one batch of the other runs."""
-    import threading
+    """Batched replicates in one batch against the same runs launched one
+    after another through the plain grid API."""
     import torch
     from paper_2404_10861_gb300 import _build, binding as hb
     _build.build()
@@ -571,36 +564,6 @@ def run_batched(args):
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
         st = b.stats()
-    # large runs apart: the small runs in one batch, the large ones beside it
-    large = [(g, kw) for g, kw in runs if kw["rows"] * kw["cols"] >= BATCH_LARGE_ISLANDS]
-    small = [(g, kw) for g, kw in runs if kw["rows"] * kw["cols"] < BATCH_LARGE_ISLANDS]
-    side = torch.cuda.Stream()
-    failure = []
-
-    def large_runs():
-        try:
-            for g, kw in large:
-                with hb.Grid(stream=side.cuda_stream, **kw) as grid:
-                    grid.run(g)
-                    grid.sync()
-        except Exception as ex:           # reported by the main thread
-            failure.append(ex)
-
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    worker = threading.Thread(target=large_runs)
-    worker.start()
-    with hb.Batch(stream=stream.cuda_stream) as b:
-        for g, kw in small:
-            b.add(g, **kw)
-        b.run(10**9)
-        stream.synchronize()
-        st_split = b.stats()
-    worker.join()
-    torch.cuda.synchronize()
-    t_split = time.perf_counter() - t0
-    if failure:
-        raise failure[0]
     # plain: one grid per run, one after another
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -620,15 +583,9 @@ def run_batched(args):
                     "agent_replications_per_s": reps / t_batch, "phases": st["phases"],
                     "kernel_launches": st["kernel_launches"],
                     "threads_per_block": st["threads_per_block"]},
-        "batched_large_apart": {
-            "seconds": t_split, "runs_per_hour": len(runs) * 3600 / t_split,
-            "agent_replications_per_s": reps / t_split, "large_runs": len(large),
-            "large_replications": sum(g * kw["rows"] * kw["cols"] * kw["n"] for g, kw in large),
-            "batch_kernel_launches": st_split["kernel_launches"]},
         "plain_sequential": {"seconds": t_plain, "runs_per_hour": len(runs) * 3600 / t_plain,
                              "agent_replications_per_s": reps / t_plain},
-        "speedup": t_plain / t_batch, "speedup_large_apart": t_plain / t_split,
-        "dtype": "u32", "data": "synthetic"}), flush=True)
+        "speedup": t_plain / t_batch, "dtype": "u32", "data": "synthetic"}), flush=True)
 
 
 def run_served(args):
