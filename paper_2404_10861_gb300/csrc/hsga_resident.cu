@@ -3,12 +3,16 @@
 // One cooperative launch advances many synchronous generations.  Each warp
 // owns IPW islands and keeps their genomes in registers for the whole launch
 // (lane l: agents l and l+32).  There is no grid-wide barrier: islands only
-// depend on their four neighbours' emigrants, so each island publishes its
-// emigrant as a record of four 64-bit words (trait, surface low, surface
-// high, direction), each word carrying the migration's sequence number in
-// its high half, into a slot double-buffered by migration parity; a
-// receiver polls the four words of each neighbour's record until all carry
-// the sequence number it expects.  A 64-bit relaxed access is single-copy
+// depend on their four neighbours' emigrants.  Multi-block grids are cut
+// into tiles of islands, one tile per block (the smallest tiles that fit:
+// 2x2 on a 64x64 grid); inside a tile the emigrants go through shared
+// memory and one block barrier per migration.  Across tiles (and, where no
+// tile shape fits, between all islands) each island publishes its emigrant
+// as a record of four 64-bit words (trait, surface low, surface high,
+// direction), each word carrying the migration's sequence number in its
+// high half, into a slot double-buffered by migration parity; a receiver
+// polls the four words of each neighbour's record until all carry the
+// sequence number it expects.  A 64-bit relaxed access is single-copy
 // atomic, so no fence or separate flag is needed: seeing the number in all
 // four words means seeing the whole record.  An island can run at most one
 // migration ahead of a neighbour, which is why two record buffers suffice: a
@@ -18,8 +22,9 @@
 // later store).
 //
 // Every wait is bounded (1 s of %globaltimer); on expiry the warp records a
-// timeout in the grid's error word and leaves, which lets its neighbours
-// time out in turn.  The cooperative launch guarantees that every island's
+// timeout in the grid's error word and leaves (in a tile: at the block's
+// next barrier, with the rest of the block), which lets its neighbours time
+// out in turn.  The cooperative launch guarantees that every island's
 // warp is resident, so waits only expire on an inconsistent state.
 #include <cuda_runtime.h>
 
