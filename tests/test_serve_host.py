@@ -243,3 +243,24 @@ def test_large_runs_one_at_a_time_and_small_ones_pass_them(fake):
     serve.serve(reqs, memory_cap=1 << 34, slice_ticks=64, large_agents=None)
     adds = [seeds[ev[2]].rid for ev in fake.log if ev[0] == "add"]
     assert adds == [0, 1, 2, 3, 4]
+
+
+def test_large_grids_count_against_the_memory_cap(fake):
+    """A large run on its own grid holds its footprint until it retires:
+    small requests that would exceed the cap beside it wait, and are
+    admitted (in arrival order) once it has finished."""
+    big, small = request(0, 0.0, 256, 150), [request(i, 0.0, 16, 40) for i in (1, 2)]
+    cap = footprint(big.config) + footprint(small[0].config)     # room for one small beside it
+    results, stats = serve.serve([big] + small, memory_cap=cap, slice_ticks=64,
+                                 large_agents=1 << 20)
+    assert sorted(r.rid for r in results) == [0, 1, 2]
+    assert stats["admissions_deferred"] > 0
+    order = [ev for ev in fake.log if ev[0] in ("grid", "add", "grid_close", "remove")]
+    seeds = [ev[1] if ev[0] in ("grid", "grid_close") else ev[2] if ev[0] == "add" else None
+             for ev in order]
+    # the second small request is admitted only after the first one retired
+    first_small_removed = next(i for i, ev in enumerate(order) if ev[0] == "remove")
+    second_small_added = next(i for i, ev in enumerate(order)
+                              if ev[0] == "add" and ev[2] == 1002)
+    assert second_small_added > first_small_removed
+    assert seeds[0] == 1000 and order[0][0] == "grid"           # the large run first
