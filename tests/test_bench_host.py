@@ -1,8 +1,9 @@
 """Host-side pieces of bench.py on CPU: the clock summary parsed from
 nvidia-smi's CSV (median SM clock, maximum, throttle reasons seen), the
 traffic figure that is read from a committed ncu summary only while the
-kernel sources still hash to the captured value, and the algorithmic bytes
-of one generation launch."""
+kernel sources still hash to the captured value, the algorithmic bytes of
+one generation launch, and the reference arm's line (the oracle on the
+host's cores)."""
 import importlib.util
 import os
 
@@ -72,3 +73,31 @@ def test_algorithmic_bytes_of_a_generation_launch(bench):
     # 12-byte genome read and child written per agent, one 12-byte emigrant
     # gather per island
     assert bench.BYTES_PER_LAUNCH == agents * 24 + 512 * 1024 * 12 == 408_944_640
+
+
+def test_reference_arm_prints_the_contract_line(bench):
+    """`--impl reference` (the oracle on the host's cores) prints one JSON
+    line with the same metric, unit and config as the GPU arm, its own
+    cpu_baseline and an e2e object without host-device bytes; other ranks of
+    a multi-process launch print nothing."""
+    import json
+    import subprocess
+    import sys
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps",
+           "1", "--warmup", "3"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "agent replications/sec"
+    assert d["unit"] == "agent replications/s" and d["higher_is_better"] is True
+    assert d["config"] == bench.config_json(1)
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] >= 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    other = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert other.returncode == 0 and not other.stdout.strip()
